@@ -1,0 +1,365 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test names the passage of arXiv:1810.07802 it checks.  None retypes the
+oracle's formulas: they check moment identities of the Appendix, exact
+algebraic identities of Sec. II.B, discrete Fourier symbols, conservation,
+closed-form flows and the numbers the paper prints.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1810_07802_gb300 import workloads as W
+
+RT = 1.0 / 3.0
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- lattice
+
+def test_lattice_matches_eq14():
+    """Eq. 14: velocities in the printed order, weights 4/9, 1/9 (odd), 1/36 (even)."""
+    ex, ey, w = O.lattice()
+    assert list(ex) == [0, 1, 1, 0, -1, -1, -1, 0, 1]
+    assert list(ey) == [0, 0, 1, 1, 1, 0, -1, -1, -1]
+    assert w[0] == pytest.approx(4 / 9, abs=0, rel=1e-15)
+    for i in range(1, 9):
+        assert w[i] == pytest.approx(1 / 9 if i % 2 else 1 / 36, rel=1e-15)
+    # Gauss-Hermite moments: sum w = 1, sum w xi xi = RT I, sum w xi^4 = 3 RT^2
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert (w * ex * ex).sum() == pytest.approx(RT, abs=1e-15)
+    assert (w * ex * ey).sum() == pytest.approx(0.0, abs=1e-15)
+    assert (w * ex ** 4).sum() == pytest.approx(3 * RT * RT, abs=1e-15)
+    assert (w * ex ** 2 * ey ** 2).sum() == pytest.approx(RT * RT, abs=1e-15)
+
+
+# ------------------------------------------------- equilibria and sources
+
+def test_f_equilibrium_and_source_moments():
+    """Appendix (A-C part): sum f_eq = phi, sum xi f_eq = phi u,
+    sum xi xi f_eq = phi RT I; sum S^f = 0 and sum xi S^f = RT theta n + d_t(phi u)."""
+    ex, ey, _ = O.lattice()
+    r = _rng(1)
+    for _ in range(50):
+        phi, ux, uy = r.uniform(-0.1, 1.1), r.uniform(-0.1, 0.1), r.uniform(-0.1, 0.1)
+        fe = O.feq(phi, ux, uy)
+        assert fe.sum() == pytest.approx(phi, abs=1e-14)
+        assert (ex * fe).sum() == pytest.approx(phi * ux, abs=1e-14)
+        assert (ey * fe).sum() == pytest.approx(phi * uy, abs=1e-14)
+        assert (ex * ex * fe).sum() == pytest.approx(phi * RT, abs=1e-14)
+        assert (ex * ey * fe).sum() == pytest.approx(0.0, abs=1e-14)
+        assert (ey * ey * fe).sum() == pytest.approx(phi * RT, abs=1e-14)
+        th = r.uniform(0, 0.25)
+        a = r.uniform(0, 2 * math.pi)
+        nx, ny = math.cos(a), math.sin(a)
+        Dx, Dy = r.uniform(-1e-3, 1e-3), r.uniform(-1e-3, 1e-3)
+        s = O.sf(th, nx, ny, Dx, Dy)
+        assert s.sum() == pytest.approx(0.0, abs=1e-15)
+        assert (ex * s).sum() == pytest.approx(RT * th * nx + Dx, abs=1e-15)
+        assert (ey * s).sum() == pytest.approx(RT * th * ny + Dy, abs=1e-15)
+
+
+def test_g_equilibrium_and_source_moments():
+    """Appendix (hydrodynamic part): sum g_eq = 0, sum xi g_eq = rho u,
+    sum xi xi g_eq = p I + rho u u; sum S^g = u.grad rho, sum xi S^g = F."""
+    ex, ey, _ = O.lattice()
+    r = _rng(2)
+    for _ in range(50):
+        p, rho = r.uniform(-1e-2, 1e-2), r.uniform(0.5, 1000)
+        ux, uy = r.uniform(-0.05, 0.05), r.uniform(-0.05, 0.05)
+        ge = O.geq(p, rho, ux, uy)
+        sc = 1e-13 * max(1.0, rho)
+        assert ge.sum() == pytest.approx(0.0, abs=sc)
+        assert (ex * ge).sum() == pytest.approx(rho * ux, abs=sc)
+        assert (ey * ge).sum() == pytest.approx(rho * uy, abs=sc)
+        assert (ex * ex * ge).sum() == pytest.approx(p + rho * ux * ux, abs=sc)
+        assert (ex * ey * ge).sum() == pytest.approx(rho * ux * uy, abs=sc)
+        assert (ey * ey * ge).sum() == pytest.approx(p + rho * uy * uy, abs=sc)
+        drx, dry = r.uniform(-300, 300), r.uniform(-300, 300)
+        Fx, Fy = r.uniform(-1e-3, 1e-3), r.uniform(-1e-3, 1e-3)
+        s = O.sg(drx, dry, Fx, Fy, ux, uy)
+        assert s.sum() == pytest.approx(ux * drx + uy * dry, abs=1e-12)
+        assert (ex * s).sum() == pytest.approx(Fx, abs=1e-12)
+        assert (ey * s).sum() == pytest.approx(Fy, abs=1e-12)
+
+
+def test_g_source_second_moment_to_leading_order():
+    """Appendix: sum xi xi S^g = uF + Fu + RT[u grad rho + grad rho u + (u.grad rho) I]
+    holds to leading order in u; the remainder must shrink at least like u^2."""
+    ex, ey, _ = O.lattice()
+    drx, dry, Fx, Fy = 0.3, -0.1, 1e-3, 2e-3
+    errs = []
+    for scale in (1.0, 0.5, 0.25):
+        ux, uy = 0.03 * scale, -0.02 * scale
+        s = O.sg(drx, dry, Fx, Fy, ux, uy)
+        udr = ux * drx + uy * dry
+        xx = (ex * ex * s).sum() - (2 * ux * Fx + RT * (2 * ux * drx + udr))
+        xy = (ex * ey * s).sum() - (ux * Fy + uy * Fx + RT * (ux * dry + uy * drx))
+        yy = (ey * ey * s).sum() - (2 * uy * Fy + RT * (2 * uy * dry + udr))
+        lead = abs(RT * udr)
+        errs.append(max(abs(xx), abs(xy), abs(yy)) / lead)
+    assert errs[0] < 0.1
+    assert errs[1] < errs[0] / 3.5 and errs[2] < errs[1] / 3.5
+
+
+# ------------------------------------------------ DUGKS algebra (Sec. II.B)
+
+def test_prestep_matches_auxiliary_definitions():
+    """Eqs. 29-30 follow from the definitions Eq. 23a (psi~), Eq. 26b (psi-bar-plus)
+    and Eq. 23b (psi~+) of the same original distribution psi."""
+    r = _rng(3)
+    for _ in range(20):
+        tau, dt = r.uniform(0.01, 3.0), r.uniform(0.1, 1.0)
+        h = dt / 2
+        psi, eq, S = r.normal(size=9), r.normal(size=9), r.normal(size=9)
+        tilde = (2 * tau + dt) / (2 * tau) * psi - dt / (2 * tau) * eq - dt / 2 * S
+        bar_plus = (2 * tau - h) / (2 * tau) * psi + h / (2 * tau) * eq + h / 2 * S
+        tilde_plus = (2 * tau - dt) / (2 * tau) * psi + dt / (2 * tau) * eq + dt / 2 * S
+        bp, tp = O.prestep(tau, dt, tilde, eq, S)
+        np.testing.assert_allclose(bp, bar_plus, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(tp, tilde_plus, rtol=0, atol=1e-13)
+
+
+def test_face_psi_inverts_bar_definition():
+    """Eq. 28 inverts the definition Eq. 26a: psi_bar = psi - h/2 (Omega + S)."""
+    r = _rng(4)
+    for _ in range(20):
+        tau, h = r.uniform(0.01, 3.0), r.uniform(0.05, 0.5)
+        psi, eq, S = r.normal(size=9), r.normal(size=9), r.normal(size=9)
+        bar = psi + h / (2 * tau) * (psi - eq) - h / 2 * S
+        np.testing.assert_allclose(O.face_psi(tau, h, bar, eq, S), psi, rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------- stencils
+
+@pytest.mark.parametrize("a,b", [(1, 0), (0, 1), (1, 2), (3, 1), (2, 3), (4, 4)])
+def test_stencil_fourier_symbols(a, b):
+    """Sec. II.B stencils on an 8x8 periodic grid against their discrete symbols:
+    the isotropic gradient has symbol i sin(kx)(2 + cos ky)/3 and the
+    nine-point Laplacian [8 cos kx + 8 cos ky + 4 cos kx cos ky - 20]/6."""
+    n = 8
+    kx, ky = 2 * math.pi * a / n, 2 * math.pi * b / n
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    phase = kx * i + ky * j
+    phi = np.cos(phase)
+    gx, gy, lp = O.grad_lap(phi)
+    np.testing.assert_allclose(gx, -np.sin(phase) * math.sin(kx) * (2 + math.cos(ky)) / 3, atol=1e-14)
+    np.testing.assert_allclose(gy, -np.sin(phase) * math.sin(ky) * (2 + math.cos(kx)) / 3, atol=1e-14)
+    sym = (8 * math.cos(kx) + 8 * math.cos(ky) + 4 * math.cos(kx) * math.cos(ky) - 20) / 6
+    np.testing.assert_allclose(lp, sym * phi, atol=1e-14)
+
+
+def test_stencils_exact_on_quadratics():
+    """Both stencils are exact for quadratic fields (away from the periodic seam)."""
+    j, i = np.meshgrid(np.arange(16.0), np.arange(16.0), indexing="ij")
+    phi = 0.3 * i * i - 0.2 * i * j + 0.1 * j * j + 0.5 * i - 0.7 * j
+    gx, gy, lp = O.grad_lap(phi)
+    sl = (slice(2, -2), slice(2, -2))
+    np.testing.assert_allclose(gx[sl], (0.6 * i - 0.2 * j + 0.5)[sl], atol=1e-12)
+    np.testing.assert_allclose(gy[sl], (-0.2 * i + 0.2 * j - 0.7)[sl], atol=1e-12)
+    np.testing.assert_allclose(lp[sl], 0.8, atol=1e-12)
+
+
+def test_wall_stencils_equal_periodic_on_mirror_extension():
+    """A no-slip wall mirrors phi into the ghost rows: the wall stencils must equal
+    the periodic stencils applied to the even extension of the field."""
+    r = _rng(5)
+    nx, ny = 7, 6
+    phi = r.uniform(size=(ny, nx))
+    ext = np.concatenate([phi, phi[::-1]], axis=0)          # period 2 ny, even about y = 0, ny
+    gx, gy, lp = O.grad_lap(phi, wall_y=True)
+    ex_, ey_, el_ = O.grad_lap(ext)
+    np.testing.assert_allclose(gx, ex_[:ny], atol=1e-15)
+    np.testing.assert_allclose(gy, ey_[:ny], atol=1e-15)
+    np.testing.assert_allclose(lp, el_[:ny], atol=1e-15)
+
+
+# -------------------------------------------------------- whole steps
+
+def test_rest_state_is_a_fixed_point():
+    """Uniform phi, u = 0, p = const: every flux cancels, the state does not move."""
+    cfg, fl = W.stationary_bubble(N=8, R=2.0)
+    phi = np.full((8, 8), 0.37)
+    o = O.Oracle(cfg, phi, p0=np.full((8, 8), 1e-3))
+    f0, g0, _ = o.state()
+    o.step(5)
+    f1, g1, _ = o.state()
+    np.testing.assert_allclose(f1, f0, atol=1e-16)
+    np.testing.assert_allclose(g1, g0, atol=1e-16)
+
+
+def test_initial_state_reproduces_macros():
+    """R7: psi~0 = psi_eq - dt/2 S reproduces phi, u and p through Eqs. 31-33
+    (exactly for u0 = 0, up to the dropped O(u F) term otherwise)."""
+    cfg, fl = W.random_state(12, 10, seed=7)
+    fl["ux0"] = None
+    fl["uy0"] = None
+    o = O.Oracle(cfg, **fl)
+    m = o.macros()
+    np.testing.assert_allclose(m["phi"], fl["phi0"], atol=1e-15)
+    np.testing.assert_allclose(m["ux"], 0, atol=1e-16)
+    np.testing.assert_allclose(m["p"], fl["p0"], atol=1e-15)
+
+
+@pytest.mark.parametrize("bc_y", ["periodic", "wall"])
+def test_phi_mass_conserved(bc_y):
+    """Finite-volume fluxes telescope and sum S^f = 0: sum phi is conserved to
+    round-off, with periodic boundaries and with no-slip walls (R9)."""
+    cfg, fl = W.random_state(19, 17, seed=11, rho_ratio=10.0, bc_y=bc_y)
+    o = O.Oracle(cfg, **fl)
+    m0 = o.macros()["phi"].sum()
+    o.step(60)
+    m1 = o.macros()["phi"].sum()
+    assert abs(m1 - m0) <= 1e-13 * abs(m0)
+    assert np.isfinite(o.state()[1]).all()
+
+
+def test_d4_symmetry_of_bubble():
+    """A centred bubble keeps the square's symmetry (x <-> y, reflections)."""
+    cfg, fl = W.stationary_bubble(N=24, R=6.0, rho_ratio=10.0)
+    o = O.Oracle(cfg, **fl)
+    o.step(40)
+    m = o.macros()
+    for k in ("phi", "p"):
+        a = m[k]
+        np.testing.assert_allclose(a, a.T, atol=1e-12)
+        np.testing.assert_allclose(a, a[::-1, :], atol=1e-12)
+        np.testing.assert_allclose(a, a[:, ::-1], atol=1e-12)
+    np.testing.assert_allclose(m["ux"], m["uy"].T, atol=1e-13)
+    np.testing.assert_allclose(m["ux"], -m["ux"][:, ::-1], atol=1e-13)
+
+
+def test_planar_tanh_is_near_steady():
+    """Eqs. 5-7: the tanh profile balances grad phi = theta n, so a slab at rest
+    only relaxes to the discrete equilibrium (O(dx^2)) and then stays put."""
+    cfg, fl = W.planar_slab(nx=64, ny=3, width=4.0, U=0.0)
+    o = O.Oracle(cfg, **fl)
+    o.step(2000)
+    a = o.macros()["phi"]
+    o.step(2000)
+    b = o.macros()["phi"]
+    assert np.abs(a - fl["phi0"]).max() < 1e-2
+    assert np.abs(b - a).max() < 2e-4
+
+
+@pytest.mark.slow
+def test_planar_translation_second_order():
+    """Sec. III.A / Fig. 1: at fixed Pe, Cn and M the translation error converges
+    at second order under grid refinement (exact solution: the shifted tanh slab)."""
+    errs = []
+    for L, wd in ((64, 4.0), (128, 8.0), (256, 16.0)):
+        Pe, M = 64.0, 0.02
+        U = Pe * M / L
+        steps = int(round(L / U / 8 / 0.5))
+        cfg, fl = W.planar_slab(nx=L, ny=3, width=wd, U=U, mobility=M)
+        o = O.Oracle(cfg, **fl)
+        o.step(steps)
+        phi = o.macros()["phi"]
+        _, ref = W.planar_slab(nx=L, ny=3, width=wd, centre=L / 2 + U * steps * 0.5)
+        errs.append(np.sqrt(((phi - ref["phi0"]) ** 2).sum() / (ref["phi0"] ** 2).sum()))
+    order = [math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])]
+    assert GOLDEN["translation_convergence_order"]["order"] == 2
+    assert min(order) > 1.85 and max(order) < 2.2, (errs, order)
+
+
+def test_circle_translation_returns():
+    """Sec. III.A (Eq. 40): after T = L0/U0 the disc is back.  E (Eq. 39) stays at
+    or below the magnitude of Table I; at T/2 the centroid has moved by (L/2, L/2)."""
+    L, U = 32, 0.02
+    cfg, fl = W.translation_circle(L=L, R=8.0, width=4.0, U=U, mobility=0.02)
+    steps = int(round(L / U / cfg["cfl"]))
+    o = O.Oracle(cfg, **fl)
+    o.step(steps // 2)
+    phi = o.macros()["phi"]
+    c = np.arange(L) + 0.5
+    cx = np.angle((phi * np.exp(2j * np.pi * c[None, :] / L)).sum()) * L / (2 * np.pi) % L
+    cy = np.angle((phi * np.exp(2j * np.pi * c[:, None] / L)).sum()) * L / (2 * np.pi) % L
+    expect = (L / 2 + U * steps // 2 * cfg["cfl"]) % L
+    for got in (cx, cy):
+        assert min(abs(got - expect), L - abs(got - expect)) < 0.1
+    o.step(steps - steps // 2)
+    phi = o.macros()["phi"]
+    E = ((phi - fl["phi0"]) ** 2).sum() / (fl["phi0"] ** 2).sum()
+    assert E < GOLDEN["table_I_translation_E_phi_vs_Pe"]["E"][0]
+    assert abs(phi.sum() - fl["phi0"].sum()) < 1e-12 * fl["phi0"].sum() * steps
+
+
+def test_taylor_green_decay():
+    """Recovered Navier-Stokes (Appendix, nu = tau_g RT): a single-phase
+    Taylor-Green vortex decays like exp(-2 nu k^2 t)."""
+    N, nu = 32, 0.1
+    cfg, fl = W.taylor_green(N=N, nu=nu)
+    o = O.Oracle(cfg, **fl)
+    m0 = o.macros()
+    steps = 400
+    o.step(steps)
+    m = o.macros()
+    amp = math.sqrt((m["ux"] ** 2).sum() / (m0["ux"] ** 2).sum())
+    k = 2 * math.pi / N
+    exact = math.exp(-2 * nu * k * k * steps * cfg["cfl"])
+    assert amp == pytest.approx(exact, rel=5e-3)
+
+
+def test_single_phase_channel_parabola():
+    """No-slip walls (R9): a body-force channel flow converges to the parabola
+    of Eq. 46 with mu_H = mu_L, to within the wall scheme's second-order error."""
+    ny = 32
+    cfg, fl = W.layered_poiseuille(ny=ny, mu_ratio=1.0, mu_h=0.1, start_from_analytic=True)
+    o = O.Oracle(cfg, **fl)
+    o.step(4000)
+    u = o.macros()["ux"][:, 0]
+    y = np.arange(ny) + 0.5
+    ua = W.poiseuille_profile(y, ny, cfg["mu_h"], cfg["mu_l"], cfg["gx"])
+    err = np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum())
+    assert err < 5e-3, err
+
+
+@pytest.mark.slow
+def test_layered_poiseuille():
+    """Sec. IV.B (Eq. 46): two-layer channel with viscosity ratio 10 reaches the
+    analytic profile within the paper's error magnitude for a coarse grid, and
+    the reciprocal viscosity rule (Eq. 35) beats the linear one (Eq. 36)."""
+    ny = 32
+    errs = {}
+    for visc in ("reciprocal", "linear"):
+        cfg, fl = W.layered_poiseuille(ny=ny, mu_ratio=10.0, start_from_analytic=True)
+        cfg["visc"] = visc
+        o = O.Oracle(cfg, **fl)
+        o.step(6000)
+        u = o.macros()["ux"][:, 0]
+        y = np.arange(ny) + 0.5
+        ua = W.poiseuille_profile(y, ny, cfg["mu_h"], cfg["mu_l"], cfg["gx"])
+        errs[visc] = np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum())
+    # the paper's coarse-grid error at mu* = 1000 is 1.4e-2 with Ny = 100;
+    # at Ny = 32 and mu* = 10 the interface occupies a larger share of the channel
+    assert errs["reciprocal"] < 5 * GOLDEN["poiseuille_L2"]["L2"][0], errs
+    assert errs["reciprocal"] < errs["linear"], errs
+
+
+@pytest.mark.slow
+def test_laplace_law():
+    """Sec. IV.A: the thermodynamic pressure P = p0 - kappa phi lap phi +
+    kappa |grad phi|^2 / 2 + p jumps by sigma / R across a bubble; the paper
+    reports ~96.5 % of the analytic value."""
+    N, R, sigma, wd = 32, 8.0, 0.01, 4.0
+    cfg, fl = W.stationary_bubble(N=N, R=R, rho_ratio=1.0, sigma=sigma, width=wd)
+    o = O.Oracle(cfg, **fl)
+    o.step(4000)
+    m = o.macros()
+    phi = m["phi"]
+    beta, kappa = 12 * sigma / wd, 1.5 * sigma * wd
+    gx, gy, lp = O.grad_lap(phi)
+    eps = beta * phi ** 2 * (phi - 1) ** 2
+    deps = beta * (2 * phi * (phi - 1) ** 2 + 2 * phi ** 2 * (phi - 1))
+    P = phi * deps - eps - kappa * phi * lp + 0.5 * kappa * (gx ** 2 + gy ** 2) + m["p"]
+    ratio = (P[N // 2, N // 2] - P[1, 1]) / (sigma / R)
+    paper = GOLDEN["laplace_ratio"]["numerical_over_analytic"]
+    assert abs(ratio - paper) < 0.09, ratio
