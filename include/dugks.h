@@ -1,0 +1,155 @@
+/*
+ * dugks.h -- C ABI of the GB300 (sm_103a) phase-field DUGKS library.
+ *
+ * The library advances the two coupled D2Q9 kinetic models of Yang, Zhong &
+ * Zhuo, "A phase-field model for large-density-ratio two-phase flows based on
+ * discrete unified gas-kinetic scheme" (arXiv:1810.07802), Sec. II.B: the
+ * conservative Allen-Cahn model for the order parameter phi (Eqs. 12, 15, 16)
+ * and the incompressible hydrodynamic model for p and u (Eqs. 13, 17-19), by
+ * the DUGKS finite-volume step (Eqs. 20-30) with the closures of Eqs. 3-10
+ * and 31-37.  Every step runs in CUDA kernels on the device; there is no CPU
+ * fallback.
+ *
+ * Conventions shared by every call
+ *  - Grid: nx * ny square cells of unit size (delta_x = 1, Sec. III); cell
+ *    (i, j) has its centre at (i + 1/2, j + 1/2).  Host fields are row-major
+ *    [ny][nx] arrays of double, x fastest, no padding.
+ *  - Lattice: D2Q9 with RT = 1/3, so xi_i = e_i and dt = CFL (Eq. 37).
+ *  - Streams: every call enqueues work on the stream given to dugks_create
+ *    (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *    Calls marked "synchronises" wait for that stream before returning.
+ *  - Errors: every call returns a dugks_status.  Invalid arguments return
+ *    DUGKS_ERR_ARG and change nothing.  The step kernels record non-finite
+ *    values (DUGKS_ERR_NONFINITE) and rho <= 0 or mu <= 0
+ *    (DUGKS_ERR_NONPHYSICAL) in a device status word; asynchronous calls
+ *    cannot see it, and the next synchronising call returns it.  The status
+ *    is sticky until dugks_destroy.
+ *  - Ownership: the library owns the handle and any device memory it
+ *    allocates.  A caller-supplied workspace stays the caller's and must
+ *    outlive the handle.  Host arrays are only read or written during the call.
+ *  - Thread safety: one handle must not be used from two host threads at once;
+ *    distinct handles are independent (their parameters are passed to the
+ *    kernels by value; no global device state).
+ */
+#ifndef DUGKS_H
+#define DUGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DUGKS_OK = 0,
+    DUGKS_ERR_ARG = -1,          /* invalid parameter or argument              */
+    DUGKS_ERR_OOM = -2,          /* device allocation failed / workspace small */
+    DUGKS_ERR_CUDA = -3,         /* a CUDA runtime call failed                 */
+    DUGKS_ERR_NONFINITE = -4,    /* a step produced NaN or Inf                 */
+    DUGKS_ERR_NONPHYSICAL = -5,  /* a step met rho <= 0 or mu <= 0             */
+    DUGKS_ERR_TIMEOUT = -6,      /* reserved for bounded device waits          */
+    DUGKS_ERR_UNSUPPORTED = -7   /* valid request this build does not provide  */
+} dugks_status;
+
+typedef enum { DUGKS_BC_PERIODIC = 0, DUGKS_BC_WALL = 1 } dugks_bc;
+typedef enum { DUGKS_FP64 = 0, DUGKS_FP32_SHIFTED = 1 } dugks_precision;
+typedef enum { DUGKS_COUPLED = 0, DUGKS_AC_PRESCRIBED_U = 1 } dugks_model;
+typedef enum { DUGKS_VISC_RECIPROCAL = 0, DUGKS_VISC_LINEAR = 1 } dugks_visc;
+
+/*
+ * Problem statement (Sec. II.A-B).  phi_H = 1 is the heavy phase, phi_L = 0
+ * the light one (Eq. 7).
+ */
+typedef struct {
+    int32_t nx, ny;        /* cells, each >= 3                                     */
+    int32_t lattice;       /* must be 9 (D2Q9, Eq. 14)                             */
+    int32_t model;         /* dugks_model: coupled (default) or Allen-Cahn only
+                              with the uniform velocity (u0x, u0y) (Sec. III)      */
+    int32_t precision;     /* dugks_precision: FP64 arithmetic and storage, or
+                              FP32 arithmetic with distributions stored in FP32
+                              as deviations from the rest state (phi_ref, p_ref) */
+    int32_t bc_x;          /* must be DUGKS_BC_PERIODIC                            */
+    int32_t bc_y;          /* periodic, or no-slip walls on y = 0 and y = ny       */
+    int32_t visc_interp;   /* dugks_visc: 1/mu linear in phi (Eq. 35) or mu (Eq. 36) */
+    int32_t gravity_mode;  /* 0: G = (gx, gy); 1: G = (rho - rho_ref)(gx, gy)      */
+    int32_t reserved;      /* must be 0                                            */
+    double cfl;            /* dt = cfl (Eq. 37 with delta_x = 1, RT = 1/3), > 0    */
+    double mobility;       /* M_phi > 0; tau_f = M_phi / RT (Eq. 34)               */
+    double width;          /* interface width W > 0 (Eq. 3)                        */
+    double rho_h, rho_l;   /* phase densities > 0 (Eq. 10); coupled model only     */
+    double mu_h, mu_l;     /* dynamic viscosities > 0 (Eqs. 35-36); coupled only   */
+    double sigma;          /* surface tension >= 0 (Eq. 3)                         */
+    double gx, gy;         /* body force (see gravity_mode), coupled model only    */
+    double rho_ref;        /* reference density for gravity_mode 1                 */
+    double phi_ref, p_ref; /* rest state subtracted before FP32 storage            */
+    double u0x, u0y;       /* prescribed velocity of the Allen-Cahn-only model     */
+} dugks_params;
+
+typedef struct dugks_ctx *dugks_handle;
+
+/* Device bytes the solver needs for these parameters (state, ping-pong
+ * buffers, macro staging, reduction scratch), or 0 if the parameters are
+ * invalid.  Used for admission by HBM footprint. */
+size_t dugks_workspace_bytes(const dugks_params *params);
+
+/* Creates a solver and builds the initial state psi~0 = psi_eq - dt/2 S with
+ * d_t(phi u) = 0 (Eq. 23a with psi = psi_eq) from host fields phi0, ux0, uy0,
+ * p0 ([ny][nx] doubles; ux0, uy0, p0 may be NULL for zero; ignored in the
+ * Allen-Cahn-only model, which uses (u0x, u0y)).
+ * device_workspace: NULL to let the library cudaMalloc its workspace, or a
+ * caller-owned device buffer of at least dugks_workspace_bytes(params) bytes,
+ * 256-byte aligned.  cuda_stream: cudaStream_t or NULL.  Synchronises. */
+dugks_status dugks_create(const dugks_params *params, const double *phi0,
+                          const double *ux0, const double *uy0, const double *p0,
+                          void *device_workspace, size_t ws_bytes,
+                          void *cuda_stream, dugks_handle *out);
+
+/* Enqueues nsteps >= 0 DUGKS time steps (Eqs. 20-30; one fused kernel launch
+ * per step).  Asynchronous. */
+dugks_status dugks_step(dugks_handle h, int64_t nsteps);
+
+/* Cell-centre macros of the current state (Eqs. 31-33): phi, p, ux, uy as
+ * [ny][nx] doubles; any pointer may be NULL.  dst_is_device != 0: pointers
+ * are device memory written on the solver's stream (asynchronous);
+ * otherwise host memory, and the call synchronises. */
+dugks_status dugks_macros(dugks_handle h, double *phi, double *p, double *ux, double *uy,
+                          int32_t dst_is_device);
+
+/* FP64 reductions on the device: total phi (phi mass), the steady-state
+ * residuals of Eq. 44 for phi and |u| against the fields at the previous
+ * dugks_reduce call (1.0 on the first call), and max |u|.  Any pointer may
+ * be NULL.  Synchronises. */
+dugks_status dugks_reduce(dugks_handle h, double *phi_mass, double *resid_phi,
+                          double *resid_u, double *umax);
+
+/* The distributions as absolute FP64 values, in the oracle-comparable layout:
+ * f [9][ny][nx], g [9][ny][nx] (zero for the Allen-Cahn-only model) and the
+ * stored (phi u)^{n-1} [2][ny][nx], on the host; any pointer may be NULL.
+ * Synchronises. */
+dugks_status dugks_get_distributions(dugks_handle h, double *f, double *g, double *phiu_prev);
+
+/* Checkpoint: size of, and copy of, the complete solver state (header,
+ * stored distributions and history exactly as held on the device).
+ * Restoring a checkpoint into a handle created with the same parameters
+ * continues bit-identically.  Both synchronise. */
+size_t dugks_state_bytes(dugks_handle h);
+dugks_status dugks_get_state(dugks_handle h, void *host_buf, size_t bytes);
+dugks_status dugks_set_state(dugks_handle h, const void *host_buf, size_t bytes);
+
+/* Number of steps taken since creation (or since the restored checkpoint's). */
+int64_t dugks_step_count(dugks_handle h);
+
+/* Waits for the solver's stream and returns the device status word. */
+dugks_status dugks_sync(dugks_handle h);
+
+/* Frees the handle and the memory the library allocated.  Synchronises. */
+dugks_status dugks_destroy(dugks_handle h);
+
+/* Static description of a status code. */
+const char *dugks_status_string(dugks_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

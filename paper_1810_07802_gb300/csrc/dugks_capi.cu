@@ -1,0 +1,463 @@
+// dugks_capi.cu -- the C ABI of include/dugks.h: parameter validation,
+// workspace layout, stream-ordered launches and host<->device transfers.
+// All arithmetic of the scheme runs in the kernels (dugks_device.cuh,
+// dugks_aux.cuh); this file only marshals.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "dugks.h"
+#include "dugks_aux.cuh"
+#include "dugks_internal.h"
+#include "dugks_reduce.cuh"
+
+using dugks::FieldArgs;
+using dugks::Phys;
+using dugks::StepArgs;
+
+namespace dugks {
+cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
+                          int have_snap, double *partial, double *out, cudaStream_t st) {
+    reduce_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(phi, ux, uy, snap, n, have_snap, partial);
+    reduce_final_kernel<<<1, 32, 0, st>>>(partial, out);
+    return cudaGetLastError();
+}
+}  // namespace dugks
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr uint64_t kStateMagic = 0x31534b4755440a31ull;  // checkpoint tag
+constexpr uint64_t kStateVersion = 1;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int nq, pitch;
+    size_t elt, plane, n;
+    size_t off_state[2], off_hist[2], off_stage, off_phid, off_snap, off_partial, off_redout, off_status, total;
+};
+
+bool valid(const dugks_params *p) {
+    if (!p) return false;
+    if (p->nx < 3 || p->ny < 3 || p->lattice != 9 || p->reserved != 0) return false;
+    if (p->model != DUGKS_COUPLED && p->model != DUGKS_AC_PRESCRIBED_U) return false;
+    if (p->precision != DUGKS_FP64 && p->precision != DUGKS_FP32_SHIFTED) return false;
+    if (p->bc_x != DUGKS_BC_PERIODIC && p->bc_x != DUGKS_BC_WALL) return false;
+    if (p->bc_y != DUGKS_BC_PERIODIC && p->bc_y != DUGKS_BC_WALL) return false;
+    if (p->visc_interp != DUGKS_VISC_RECIPROCAL && p->visc_interp != DUGKS_VISC_LINEAR) return false;
+    if (p->gravity_mode != 0 && p->gravity_mode != 1) return false;
+    auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
+    auto fin = [](double v) { return std::isfinite(v); };
+    if (!pos(p->cfl) || !pos(p->mobility) || !pos(p->width)) return false;
+    if (!fin(p->phi_ref) || !fin(p->p_ref) || !fin(p->u0x) || !fin(p->u0y)) return false;
+    if (p->model == DUGKS_COUPLED) {
+        if (!pos(p->rho_h) || !pos(p->rho_l) || !pos(p->mu_h) || !pos(p->mu_l)) return false;
+        if (!fin(p->sigma) || p->sigma < 0.0 || !fin(p->gx) || !fin(p->gy) || !fin(p->rho_ref)) return false;
+    }
+    // grid dimensions of the kernels and 64-bit sizes
+    if ((long long)p->nx * p->ny > (1ll << 40)) return false;
+    return true;
+}
+
+Layout layout(const dugks_params *p) {
+    Layout L;
+    L.nq = p->model == DUGKS_COUPLED ? 18 : 9;
+    L.elt = p->precision == DUGKS_FP64 ? 8 : 4;
+    L.pitch = (int)align_up((size_t)p->nx, 32);  // 128-byte (FP32) / 256-byte (FP64) rows
+    L.plane = (size_t)L.pitch * (size_t)p->ny;
+    L.n = (size_t)p->nx * (size_t)p->ny;
+    size_t o = 0;
+    for (int b = 0; b < 2; b++) {
+        L.off_state[b] = o;
+        o = align_up(o + (size_t)L.nq * L.plane * L.elt, kAlign);
+    }
+    for (int b = 0; b < 2; b++) {
+        L.off_hist[b] = o;
+        o = align_up(o + 2 * L.plane * L.elt, kAlign);
+    }
+    L.off_stage = o;   o = align_up(o + 4 * L.n * sizeof(double), kAlign);
+    L.off_phid = o;    o = align_up(o + L.n * sizeof(double), kAlign);
+    L.off_snap = o;    o = align_up(o + 3 * L.n * sizeof(double), kAlign);
+    L.off_partial = o; o = align_up(o + (size_t)dugks::RED_BLOCKS * dugks::RED_VALS * sizeof(double), kAlign);
+    L.off_redout = o;  o = align_up(o + 8 * sizeof(double), kAlign);
+    L.off_status = o;  o = align_up(o + sizeof(unsigned), kAlign);
+    L.total = o;
+    return L;
+}
+
+template <typename Real>
+Phys<Real> make_phys(const dugks_params &p) {
+    Phys<Real> ph;
+    std::memset(&ph, 0, sizeof ph);
+    const double dt = p.cfl, h = 0.5 * dt, tau = p.mobility * 3.0;  // tau_f = M / RT (Eq. 34)
+    ph.dt = Real(dt);
+    ph.h = Real(h);
+    ph.half_dt = Real(0.5 * dt);
+    ph.half_h = Real(0.5 * h);
+    ph.pf_a = Real((2 * tau - h) / (2 * tau + dt));  // Eq. 29
+    ph.pf_b = Real(3 * h / (2 * tau + dt));
+    ph.pf_c = Real(3 * tau * h / (2 * tau + dt));
+    ph.ff_a = Real(2 * tau / (2 * tau + h));         // Eq. 28
+    ph.ff_b = Real(h / (2 * tau + h));
+    ph.ff_c = Real(tau * h / (2 * tau + h));
+    ph.beta4 = Real(4.0 * 12.0 * p.sigma / p.width); // Eq. 3
+    ph.kappa = Real(1.5 * p.sigma * p.width);
+    ph.theta_k = Real(4.0 / p.width);                // Eq. 6 with phi_H = 1, phi_L = 0
+    if (p.model == DUGKS_COUPLED) {
+        ph.drho = Real(p.rho_h - p.rho_l);
+        ph.rho_l = Real(p.rho_l);
+        if (p.visc_interp == DUGKS_VISC_LINEAR) {
+            ph.visc_a = Real(p.mu_h - p.mu_l);
+            ph.visc_b = Real(p.mu_l);
+        } else {
+            ph.visc_a = Real(1.0 / p.mu_h - 1.0 / p.mu_l);
+            ph.visc_b = Real(1.0 / p.mu_l);
+        }
+        ph.gx = Real(p.gx);
+        ph.gy = Real(p.gy);
+        ph.rho_ref = Real(p.rho_ref);
+    }
+    ph.phi_ref = Real(p.phi_ref);
+    ph.p_ref = Real(p.p_ref);
+    ph.u0x = Real(p.u0x);
+    ph.u0y = Real(p.u0y);
+    ph.visc_linear = p.visc_interp == DUGKS_VISC_LINEAR;
+    ph.grav_mode = p.gravity_mode;
+    return ph;
+}
+
+dugks_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return DUGKS_OK;
+    return e == cudaErrorMemoryAllocation ? DUGKS_ERR_OOM : DUGKS_ERR_CUDA;
+}
+
+}  // namespace
+
+struct dugks_ctx {
+    dugks_params P;
+    Layout L;
+    bool fp32, coupled, wally;
+    cudaStream_t st;
+    unsigned char *ws;
+    bool owns;
+    int cur;
+    int64_t steps;
+    int have_snap;
+    unsigned status_seen;
+    Phys<double> phd;
+    Phys<float> phf;
+
+    void *state(int b) const { return ws + L.off_state[b]; }
+    void *hist(int b) const { return ws + L.off_hist[b]; }
+    double *stage() const { return reinterpret_cast<double *>(ws + L.off_stage); }
+    double *phid() const { return reinterpret_cast<double *>(ws + L.off_phid); }
+    double *snap() const { return reinterpret_cast<double *>(ws + L.off_snap); }
+    double *partial() const { return reinterpret_cast<double *>(ws + L.off_partial); }
+    double *redout() const { return reinterpret_cast<double *>(ws + L.off_redout); }
+    unsigned *status() const { return reinterpret_cast<unsigned *>(ws + L.off_status); }
+
+    template <typename Real>
+    FieldArgs<Real> fields() const {
+        FieldArgs<Real> a;
+        a.state = static_cast<const Real *>(state(cur));
+        a.hist = static_cast<const Real *>(hist(cur));
+        a.nx = P.nx;
+        a.ny = P.ny;
+        a.pitch = L.pitch;
+        a.plane = (long long)L.plane;
+        return a;
+    }
+};
+
+namespace {
+
+// Waits for the stream and folds the device status word into a status code.
+dugks_status sync_status(dugks_ctx *c) {
+    unsigned s = 0;
+    cudaError_t e = cudaMemcpyAsync(&s, c->status(), sizeof s, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    c->status_seen |= s;
+    if (c->status_seen & dugks::STATUS_NONFINITE) return DUGKS_ERR_NONFINITE;
+    if (c->status_seen & dugks::STATUS_NONPHYSICAL) return DUGKS_ERR_NONPHYSICAL;
+    return DUGKS_OK;
+}
+
+cudaError_t run_macros(dugks_ctx *c, double *ophi, double *op, double *oux, double *ouy) {
+    if (c->fp32)
+        return dugks::launch_macros<float>(c->fields<float>(), c->phid(), c->phd, c->coupled, c->wally, ophi, op, oux,
+                                           ouy, c->st);
+    return dugks::launch_macros<double>(c->fields<double>(), c->phid(), c->phd, c->coupled, c->wally, ophi, op, oux,
+                                        ouy, c->st);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t dugks_workspace_bytes(const dugks_params *params) {
+    if (!valid(params)) return 0;
+    return layout(params).total;
+}
+
+dugks_status dugks_create(const dugks_params *params, const double *phi0, const double *ux0, const double *uy0,
+                          const double *p0, void *device_workspace, size_t ws_bytes, void *cuda_stream,
+                          dugks_handle *out) {
+    if (!out) return DUGKS_ERR_ARG;
+    *out = nullptr;
+    if (!valid(params) || !phi0) return DUGKS_ERR_ARG;
+    if (params->bc_x != DUGKS_BC_PERIODIC) return DUGKS_ERR_UNSUPPORTED;
+    const Layout L = layout(params);
+    if (device_workspace && (reinterpret_cast<uintptr_t>(device_workspace) % kAlign)) return DUGKS_ERR_ARG;
+    if (device_workspace && ws_bytes < L.total) return DUGKS_ERR_OOM;
+
+    dugks_ctx *c = new (std::nothrow) dugks_ctx();
+    if (!c) return DUGKS_ERR_OOM;
+    c->P = *params;
+    c->L = L;
+    c->fp32 = params->precision == DUGKS_FP32_SHIFTED;
+    c->coupled = params->model == DUGKS_COUPLED;
+    c->wally = params->bc_y == DUGKS_BC_WALL;
+    c->st = static_cast<cudaStream_t>(cuda_stream);
+    c->cur = 0;
+    c->steps = 0;
+    c->have_snap = 0;
+    c->status_seen = 0;
+    c->phd = make_phys<double>(*params);
+    c->phf = make_phys<float>(*params);
+    if (device_workspace) {
+        c->ws = static_cast<unsigned char *>(device_workspace);
+        c->owns = false;
+    } else {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, L.total);
+        if (e != cudaSuccess) {
+            delete c;
+            return from_cuda(e);
+        }
+        c->ws = static_cast<unsigned char *>(p);
+        c->owns = true;
+    }
+
+    cudaError_t e = cudaMemsetAsync(c->ws, 0, L.off_stage, c->st);  // state, history (incl. row padding)
+    const size_t fb = L.n * sizeof(double);
+    double *in = c->stage();
+    const double *src[4] = {phi0, ux0, uy0, p0};
+    for (int i = 0; i < 4 && e == cudaSuccess; i++) {
+        if (src[i] && (i == 0 || c->coupled))
+            e = cudaMemcpyAsync(in + i * L.n, src[i], fb, cudaMemcpyHostToDevice, c->st);
+        else
+            e = cudaMemsetAsync(in + i * L.n, 0, fb, c->st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status(), 0, sizeof(unsigned), c->st);
+    if (e == cudaSuccess) {
+        if (c->fp32)
+            e = dugks::launch_init<float>(in, static_cast<float *>(c->state(0)), static_cast<float *>(c->hist(0)),
+                                          params->nx, params->ny, L.pitch, (long long)L.plane, c->phd, c->coupled,
+                                          c->wally, c->st);
+        else
+            e = dugks::launch_init<double>(in, static_cast<double *>(c->state(0)), static_cast<double *>(c->hist(0)),
+                                           params->nx, params->ny, L.pitch, (long long)L.plane, c->phd, c->coupled,
+                                           c->wally, c->st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        if (c->owns) cudaFree(c->ws);
+        delete c;
+        return from_cuda(e);
+    }
+    *out = c;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
+    if (!c || nsteps < 0) return DUGKS_ERR_ARG;
+    for (int64_t n = 0; n < nsteps; n++) {
+        cudaError_t e;
+        const int nxt = c->cur ^ 1;
+        if (c->fp32) {
+            StepArgs<float> a;
+            a.src = static_cast<const float *>(c->state(c->cur));
+            a.dst = static_cast<float *>(c->state(nxt));
+            a.hsrc = static_cast<const float *>(c->hist(c->cur));
+            a.hdst = static_cast<float *>(c->hist(nxt));
+            a.nx = c->P.nx;
+            a.ny = c->P.ny;
+            a.pitch = c->L.pitch;
+            a.plane = (long long)c->L.plane;
+            a.first_step = c->steps == 0;
+            a.status = c->status();
+            e = dugks::launch_step<float>(a, c->phf, c->coupled, c->wally, c->st);
+        } else {
+            StepArgs<double> a;
+            a.src = static_cast<const double *>(c->state(c->cur));
+            a.dst = static_cast<double *>(c->state(nxt));
+            a.hsrc = static_cast<const double *>(c->hist(c->cur));
+            a.hdst = static_cast<double *>(c->hist(nxt));
+            a.nx = c->P.nx;
+            a.ny = c->P.ny;
+            a.pitch = c->L.pitch;
+            a.plane = (long long)c->L.plane;
+            a.first_step = c->steps == 0;
+            a.status = c->status();
+            e = dugks::launch_step<double>(a, c->phd, c->coupled, c->wally, c->st);
+        }
+        if (e != cudaSuccess) return from_cuda(e);
+        c->cur = nxt;
+        c->steps++;
+    }
+    return DUGKS_OK;
+}
+
+dugks_status dugks_macros(dugks_handle c, double *phi, double *p, double *ux, double *uy, int32_t dst_is_device) {
+    if (!c) return DUGKS_ERR_ARG;
+    cudaError_t e;
+    if (dst_is_device) {
+        e = run_macros(c, phi, p, ux, uy);
+        return from_cuda(e);
+    }
+    double *s = c->stage();
+    const size_t n = c->L.n;
+    e = run_macros(c, s, s + n, s + 2 * n, s + 3 * n);
+    double *dst[4] = {phi, p, ux, uy};
+    for (int i = 0; i < 4 && e == cudaSuccess; i++)
+        if (dst[i]) e = cudaMemcpyAsync(dst[i], s + i * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(c);
+}
+
+dugks_status dugks_reduce(dugks_handle c, double *phi_mass, double *resid_phi, double *resid_u, double *umax) {
+    if (!c) return DUGKS_ERR_ARG;
+    double *s = c->stage();
+    const size_t n = c->L.n;
+    cudaError_t e = run_macros(c, s, s + n, s + 2 * n, s + 3 * n);
+    if (e == cudaSuccess)
+        e = dugks::launch_reduce(s, s + 2 * n, s + 3 * n, c->snap(), (long long)n, c->have_snap, c->partial(),
+                                 c->redout(), c->st);
+    double r[dugks::RED_VALS];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r, c->redout(), sizeof r, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->snap(), s, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->snap() + n, s + 2 * n, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    dugks_status st = sync_status(c);
+    if (phi_mass) *phi_mass = r[0];
+    if (resid_phi) *resid_phi = c->have_snap ? (r[1] > 0 ? r[2] / r[1] : 0.0) : 1.0;
+    if (resid_u) *resid_u = c->have_snap ? (r[3] > 0 ? r[4] / r[3] : 0.0) : 1.0;
+    if (umax) *umax = r[5];
+    c->have_snap = 1;
+    return st;
+}
+
+dugks_status dugks_get_distributions(dugks_handle c, double *f, double *g, double *phiu_prev) {
+    if (!c) return DUGKS_ERR_ARG;
+    const size_t n = c->L.n;
+    const int nq = c->L.nq;
+    double *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)(nq + 2) * n * sizeof(double), c->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (c->fp32)
+        e = dugks::launch_export<float>(c->fields<float>(), nq, c->P.phi_ref, c->P.p_ref, tmp, tmp + nq * n, c->st);
+    else
+        e = dugks::launch_export<double>(c->fields<double>(), nq, c->P.phi_ref, c->P.p_ref, tmp, tmp + nq * n, c->st);
+    if (e == cudaSuccess && f) e = cudaMemcpyAsync(f, tmp, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && g) {
+        if (c->coupled)
+            e = cudaMemcpyAsync(g, tmp + 9 * n, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+        else
+            std::memset(g, 0, 9 * n * sizeof(double));
+    }
+    if (e == cudaSuccess && phiu_prev)
+        e = cudaMemcpyAsync(phiu_prev, tmp + nq * n, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    cudaError_t e2 = cudaFreeAsync(tmp, c->st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(c);
+}
+
+namespace {
+struct StateHeader {
+    uint64_t magic, version, nx, ny, nq, elt, model, precision, bc_y, steps;
+};
+}  // namespace
+
+size_t dugks_state_bytes(dugks_handle c) {
+    if (!c) return 0;
+    return sizeof(StateHeader) + (size_t)(c->L.nq + 2) * c->L.n * c->L.elt;
+}
+
+dugks_status dugks_get_state(dugks_handle c, void *host_buf, size_t bytes) {
+    if (!c || !host_buf || bytes < dugks_state_bytes(c)) return DUGKS_ERR_ARG;
+    StateHeader hd = {kStateMagic, kStateVersion, (uint64_t)c->P.nx, (uint64_t)c->P.ny, (uint64_t)c->L.nq,
+                      (uint64_t)c->L.elt, (uint64_t)c->P.model, (uint64_t)c->P.precision, (uint64_t)c->P.bc_y,
+                      (uint64_t)c->steps};
+    std::memcpy(host_buf, &hd, sizeof hd);
+    unsigned char *dst = static_cast<unsigned char *>(host_buf) + sizeof hd;
+    const size_t row = (size_t)c->P.nx * c->L.elt, dp = (size_t)c->L.pitch * c->L.elt;
+    cudaError_t e = cudaMemcpy2DAsync(dst, row, c->state(c->cur), dp, row, (size_t)c->L.nq * c->P.ny,
+                                      cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dst + (size_t)c->L.nq * c->L.n * c->L.elt, row, c->hist(c->cur), dp, row,
+                              (size_t)2 * c->P.ny, cudaMemcpyDeviceToHost, c->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(c);
+}
+
+dugks_status dugks_set_state(dugks_handle c, const void *host_buf, size_t bytes) {
+    if (!c || !host_buf || bytes < dugks_state_bytes(c)) return DUGKS_ERR_ARG;
+    StateHeader hd;
+    std::memcpy(&hd, host_buf, sizeof hd);
+    if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.nx != (uint64_t)c->P.nx ||
+        hd.ny != (uint64_t)c->P.ny || hd.nq != (uint64_t)c->L.nq || hd.elt != (uint64_t)c->L.elt ||
+        hd.model != (uint64_t)c->P.model || hd.precision != (uint64_t)c->P.precision ||
+        hd.bc_y != (uint64_t)c->P.bc_y)
+        return DUGKS_ERR_ARG;
+    const unsigned char *src = static_cast<const unsigned char *>(host_buf) + sizeof hd;
+    const size_t row = (size_t)c->P.nx * c->L.elt, dp = (size_t)c->L.pitch * c->L.elt;
+    cudaError_t e = cudaMemcpy2DAsync(c->state(c->cur), dp, src, row, row, (size_t)c->L.nq * c->P.ny,
+                                      cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(c->hist(c->cur), dp, src + (size_t)c->L.nq * c->L.n * c->L.elt, row, row,
+                              (size_t)2 * c->P.ny, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    c->steps = (int64_t)hd.steps;
+    c->have_snap = 0;
+    return DUGKS_OK;
+}
+
+int64_t dugks_step_count(dugks_handle c) { return c ? c->steps : -1; }
+
+dugks_status dugks_sync(dugks_handle c) {
+    if (!c) return DUGKS_ERR_ARG;
+    return sync_status(c);
+}
+
+dugks_status dugks_destroy(dugks_handle c) {
+    if (!c) return DUGKS_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (c->owns) {
+        cudaError_t e2 = cudaFree(c->ws);
+        if (e == cudaSuccess) e = e2;
+    }
+    delete c;
+    return from_cuda(e);
+}
+
+const char *dugks_status_string(dugks_status s) {
+    switch (s) {
+    case DUGKS_OK: return "ok";
+    case DUGKS_ERR_ARG: return "invalid argument";
+    case DUGKS_ERR_OOM: return "out of device memory or workspace too small";
+    case DUGKS_ERR_CUDA: return "CUDA runtime error";
+    case DUGKS_ERR_NONFINITE: return "non-finite value produced by a step";
+    case DUGKS_ERR_NONPHYSICAL: return "non-physical density or viscosity (<= 0)";
+    case DUGKS_ERR_TIMEOUT: return "device wait timed out";
+    case DUGKS_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+"""Python binding of the C ABI in include/dugks.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library; this module converts a
+workload dictionary (see `workloads`) into `dugks_params`, hands device memory
+(a torch uint8 workspace) and the current torch stream to the library, and
+copies host arrays in and out.  If the library is missing the import fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class DugksParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("lattice", ctypes.c_int32),
+        ("model", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("visc_interp", ctypes.c_int32), ("gravity_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("cfl", ctypes.c_double), ("mobility", ctypes.c_double), ("width", ctypes.c_double),
+        ("rho_h", ctypes.c_double), ("rho_l", ctypes.c_double),
+        ("mu_h", ctypes.c_double), ("mu_l", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("rho_ref", ctypes.c_double),
+        ("phi_ref", ctypes.c_double), ("p_ref", ctypes.c_double),
+        ("u0x", ctypes.c_double), ("u0y", ctypes.c_double),
+    ]
+
+
+STATUS = {0: "DUGKS_OK", -1: "DUGKS_ERR_ARG", -2: "DUGKS_ERR_OOM", -3: "DUGKS_ERR_CUDA",
+          -4: "DUGKS_ERR_NONFINITE", -5: "DUGKS_ERR_NONPHYSICAL", -6: "DUGKS_ERR_TIMEOUT",
+          -7: "DUGKS_ERR_UNSUPPORTED"}
+
+# Every symbol include/dugks.h declares, with (restype, argtypes).
+SIGNATURES = {
+    "dugks_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(DugksParams)]),
+    "dugks_create": (ctypes.c_int, [ctypes.POINTER(DugksParams), _dp, _dp, _dp, _dp, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "dugks_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "dugks_macros": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp, ctypes.c_int32]),
+    "dugks_reduce": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
+    "dugks_get_distributions": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp]),
+    "dugks_state_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "dugks_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "dugks_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "dugks_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "dugks_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "dugks_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "dugks_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+class DugksError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = lib().dugks_status_string(code).decode() if _lib is not None else ""
+        super().__init__("%s failed: %s (%s)" % (what, STATUS.get(code, code), msg))
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB_PATH
+
+
+def lib(build_if_missing=False):
+    """Load the CUDA library.  Raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB_PATH
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise ImportError("CUDA library %s is not built; run __graft_entry__.build()" % path)
+            _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, what):
+    if code != 0:
+        raise DugksError(code, what)
+
+
+_ENUM = {
+    "model": {"coupled": 0, "ac": 1},
+    "precision": {"fp64": 0, "fp32": 1},
+    "bc": {"periodic": 0, "wall": 1},
+    "visc": {"reciprocal": 0, "linear": 1},
+}
+
+
+def make_params(cfg):
+    p = DugksParams()
+    p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
+    p.lattice = 9
+    p.model = _ENUM["model"][cfg.get("model", "coupled")]
+    p.precision = _ENUM["precision"][cfg.get("precision", "fp64")]
+    p.bc_x = _ENUM["bc"][cfg.get("bc_x", "periodic")]
+    p.bc_y = _ENUM["bc"][cfg.get("bc_y", "periodic")]
+    p.visc_interp = _ENUM["visc"][cfg.get("visc", "reciprocal")]
+    p.gravity_mode = int(cfg.get("gravity_mode", 0))
+    p.reserved = 0
+    for k in ("cfl", "mobility", "width", "rho_h", "rho_l", "mu_h", "mu_l", "sigma", "gx", "gy",
+              "rho_ref", "phi_ref", "p_ref", "u0x", "u0y"):
+        setattr(p, k, float(cfg.get(k, 0.0)))
+    if p.precision == 0:
+        # the FP64 path keeps absolute distributions unless asked otherwise
+        p.phi_ref = float(cfg.get("phi_ref_fp64", 0.0))
+        p.p_ref = float(cfg.get("p_ref_fp64", 0.0))
+    return p
+
+
+def workspace_bytes(cfg):
+    return int(lib().dugks_workspace_bytes(ctypes.byref(make_params(cfg))))
+
+
+def _host(a, shape):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(shape)
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+class Solver:
+    """One DUGKS problem resident on the GPU.
+
+    workspace: "torch" (a torch.uint8 CUDA tensor owned by this object),
+    "library" (cudaMalloc inside the library) or a caller tensor.
+    stream: a torch.cuda.Stream, or None for torch's current stream.
+    """
+
+    def __init__(self, cfg, phi0, ux0=None, uy0=None, p0=None, workspace="torch", stream=None, device=None):
+        import torch
+
+        self.cfg = dict(cfg)
+        self.params = make_params(cfg)
+        self.nx, self.ny = self.params.nx, self.params.ny
+        L = lib()
+        need = int(L.dugks_workspace_bytes(ctypes.byref(self.params)))
+        if need == 0:
+            raise DugksError(-1, "dugks_workspace_bytes")
+        self.device = torch.device("cuda" if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._ws = None
+        ws_ptr, ws_len = None, 0
+        if isinstance(workspace, str) and workspace == "torch":
+            self._ws = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+            base = self._ws.data_ptr()
+            ws_ptr = (base + 255) // 256 * 256
+            ws_len = need
+        elif isinstance(workspace, str) and workspace == "library":
+            pass
+        else:
+            self._ws = workspace
+            ws_ptr, ws_len = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+        shp = (self.ny, self.nx)
+        arrs = [_host(phi0, shp), _host(ux0, shp), _host(uy0, shp), _host(p0, shp)]
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            code = L.dugks_create(ctypes.byref(self.params), *[_ptr(a) for a in arrs],
+                                  ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_len,
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _check(code, "dugks_create")
+        self.h = h
+        self.workspace_bytes = need
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            code = lib().dugks_destroy(self.h)
+            self.h = None
+            _check(code, "dugks_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- stepping
+    def step(self, n=1):
+        _check(lib().dugks_step(self.h, int(n)), "dugks_step")
+
+    @property
+    def step_count(self):
+        return int(lib().dugks_step_count(self.h))
+
+    def sync(self):
+        _check(lib().dugks_sync(self.h), "dugks_sync")
+
+    # -- outputs
+    def macros(self):
+        shp = (self.ny, self.nx)
+        out = {k: np.empty(shp) for k in ("phi", "p", "ux", "uy")}
+        _check(lib().dugks_macros(self.h, *[_ptr(out[k]) for k in ("phi", "p", "ux", "uy")], 0), "dugks_macros")
+        return out
+
+    def macros_device(self, out):
+        """Write phi, p, ux, uy into CUDA float64 tensors of shape (ny, nx) (dict; missing keys skipped)."""
+        ptrs = []
+        for k in ("phi", "p", "ux", "uy"):
+            t = out.get(k)
+            ptrs.append(None if t is None else ctypes.cast(t.data_ptr(), _dp))
+        _check(lib().dugks_macros(self.h, *ptrs, 1), "dugks_macros")
+
+    def reduce(self):
+        v = [ctypes.c_double() for _ in range(4)]
+        _check(lib().dugks_reduce(self.h, *[ctypes.byref(x) for x in v]), "dugks_reduce")
+        return tuple(x.value for x in v)
+
+    def distributions(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((9, self.ny, self.nx))
+        hh = np.empty((2, self.ny, self.nx))
+        _check(lib().dugks_get_distributions(self.h, _ptr(f), _ptr(g), _ptr(hh)), "dugks_get_distributions")
+        return f, g, hh
+
+    def get_state(self):
+        n = int(lib().dugks_state_bytes(self.h))
+        buf = np.empty(n, dtype=np.uint8)
+        _check(lib().dugks_get_state(self.h, buf.ctypes.data_as(ctypes.c_void_p), n), "dugks_get_state")
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().dugks_set_state(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.size), "dugks_set_state")

@@ -151,12 +151,13 @@ def taylor_green(N=32, U=1e-3, nu=0.1, cfl=0.5):
 
 def random_state(nx, ny, seed=1, rho_ratio=1000.0, model="coupled", bc_y="periodic",
                  amplitude=0.3, velocity=1e-3):
-    """A rough, asymmetric coupled state for parity tests: random phi around 0.5
-    plus a bubble, small random velocities and pressure."""
+    """A rough, asymmetric coupled state for parity tests: an off-centre bubble
+    with phi kept inside (0.03, 0.97) (so rho > 0 at any density ratio), plus
+    cell noise, small random velocities and pressure."""
     u = splitmix64_uniform(seed, 4 * nx * ny).reshape(4, ny, nx)
     X, Y = _centres(nx, ny)
     r = np.hypot(X - 0.4 * nx, Y - 0.55 * ny)
-    phi = _tanh_profile(r - 0.25 * min(nx, ny), 3.0) + amplitude * (u[0] - 0.5) * 0.2
+    phi = 0.05 + 0.9 * _tanh_profile(r - 0.25 * min(nx, ny), 3.0) + amplitude * (u[0] - 0.5) * 0.1
     ux = velocity * (2 * u[1] - 1)
     uy = velocity * (2 * u[2] - 1)
     p = 1e-4 * (2 * u[3] - 1)

@@ -1,0 +1,74 @@
+"""The C-ABI library loads, exports every symbol include/dugks.h declares, and
+rejects invalid problems before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1810_07802_gb300 import build as gpu_build
+from paper_1810_07802_gb300 import solver, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gpu_build.build()
+    return solver.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "dugks.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dugks_[a-z_]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(solver.SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_params_struct_size_matches_header():
+    # 10 int32 fields followed by 15 doubles, no padding
+    assert ctypes.sizeof(solver.DugksParams) == 10 * 4 + 15 * 8
+
+
+def test_workspace_bytes_and_validation(lib):
+    cfg, _ = workloads.spinodal(N=64)
+    ws64 = solver.workspace_bytes(dict(cfg, precision="fp64"))
+    ws32 = solver.workspace_bytes(dict(cfg, precision="fp32"))
+    assert ws64 > ws32 > 0
+    # two ping-pong copies of 18 distributions and 2 history planes, 64-column pitch
+    assert ws64 >= 2 * 20 * 64 * 64 * 8
+    bad = [dict(cfg, nx=2), dict(cfg, ny=0), dict(cfg, cfl=0.0), dict(cfg, mobility=-1.0),
+           dict(cfg, width=0.0), dict(cfg, rho_l=0.0), dict(cfg, mu_h=float("nan")), dict(cfg, sigma=-1.0)]
+    for b in bad:
+        assert solver.workspace_bytes(b) == 0, b
+    p = solver.make_params(cfg)
+    p.lattice = 8
+    assert lib.dugks_workspace_bytes(ctypes.byref(p)) == 0
+
+
+def test_create_rejects_invalid_without_gpu(lib):
+    import numpy as np
+
+    cfg, f = workloads.spinodal(N=16)
+    h = ctypes.c_void_p()
+    phi = np.ascontiguousarray(f["phi0"])
+    dp = ctypes.POINTER(ctypes.c_double)
+    p = solver.make_params(dict(cfg, nx=2))
+    assert lib.dugks_create(ctypes.byref(p), phi.ctypes.data_as(dp), None, None, None, None, 0, None,
+                            ctypes.byref(h)) == -1
+    p = solver.make_params(dict(cfg, bc_x="wall"))
+    assert lib.dugks_create(ctypes.byref(p), phi.ctypes.data_as(dp), None, None, None, None, 0, None,
+                            ctypes.byref(h)) == -7
+    p = solver.make_params(cfg)
+    assert lib.dugks_create(ctypes.byref(p), None, None, None, None, None, 0, None, ctypes.byref(h)) == -1
+    assert lib.dugks_step(None, 1) == -1
+    assert lib.dugks_step_count(None) == -1
+    assert lib.dugks_status_string(-4) == b"non-finite value produced by a step"

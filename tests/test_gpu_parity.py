@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 bar: max |GPU - oracle| <= 1e-10 on phi, p, u (and on the stored
+distributions) after the configured steps, on identical seeded inputs.
+Sizes span several tiles and ragged tails (FP64 tiles are 16 x 16, FP32
+tiles 32 x 8), tiny grids smaller than one tile, and walls.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_1810_07802_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1810_07802_gb300 import build, solver
+
+    build.build()
+    solver.lib()
+    return solver
+
+
+def run_both(S, cfg, fields, steps):
+    with S.Solver(cfg, **fields) as s:
+        s.step(steps)
+        got = s.macros()
+        dist = s.distributions()
+    o = Oracle(cfg, **fields)
+    o.step(steps)
+    return got, o.macros(), dist, o.state()
+
+
+def assert_parity(got, ref, dist=None, state=None, tol=TOL, what=""):
+    for k in ("phi", "p", "ux", "uy"):
+        err = np.abs(got[k] - ref[k]).max()
+        assert err <= tol, "%s %s: max err %.3e" % (what, k, err)
+    if dist is not None:
+        for name, a, b in zip(("f", "g", "phiu"), dist, state):
+            err = np.abs(a - b).max()
+            assert err <= tol, "%s %s: max err %.3e" % (what, name, err)
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(37, 29, 1), (37, 29, 12), (16, 16, 3), (3, 3, 4),
+                                         (5, 40, 6), (70, 9, 5), (33, 17, 20)])
+def test_coupled_periodic_fp64(S, nx, ny, steps):
+    cfg, f = W.random_state(nx, ny, seed=nx * 100 + ny)
+    got, ref, dist, st = run_both(S, cfg, f, steps)
+    assert_parity(got, ref, dist, st, what="%dx%d/%d" % (nx, ny, steps))
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(37, 29, 8), (20, 3, 5), (17, 33, 10), (40, 4, 3)])
+def test_coupled_walls_fp64(S, nx, ny, steps):
+    cfg, f = W.random_state(nx, ny, seed=7 + nx, bc_y="wall")
+    got, ref, dist, st = run_both(S, cfg, f, steps)
+    assert_parity(got, ref, dist, st, what="walls %dx%d" % (nx, ny))
+
+
+@pytest.mark.parametrize("visc,grav", [("linear", 0), ("reciprocal", 0), ("linear", 1)])
+def test_closure_options_fp64(S, visc, grav):
+    cfg, f = W.random_state(24, 20, seed=5)
+    cfg.update(visc=visc, gravity_mode=grav)
+    got, ref, dist, st = run_both(S, cfg, f, 6)
+    assert_parity(got, ref, dist, st, what="%s/%d" % (visc, grav))
+
+
+@pytest.mark.parametrize("bc_y", ["periodic", "wall"])
+def test_allen_cahn_only_fp64(S, bc_y):
+    cfg, f = W.translation_circle(L=40, R=10.0, U=0.02)
+    cfg["bc_y"] = bc_y
+    got, ref, dist, st = run_both(S, cfg, f, 25)
+    assert_parity(got, ref, dist, st, what="A-C " + bc_y)
+
+
+def test_paper_workloads_fp64(S):
+    """Reduced-size versions of the paper's problems: bubble, Poiseuille, RTI."""
+    cases = [W.stationary_bubble(N=48, R=12.0, rho_ratio=1000.0),
+             W.layered_poiseuille(ny=40, nx=4, mu_ratio=100.0),
+             W.rayleigh_taylor(L=32, ny=64),
+             W.taylor_green(N=32)]
+    for cfg, f in cases:
+        got, ref, dist, st = run_both(S, cfg, f, 30)
+        assert_parity(got, ref, dist, st, what=str(cfg["nx"]) + "x" + str(cfg["ny"]))
+
+
+def test_spinodal_full_size_one_step_fp64(S):
+    """The 2048^2 spinodal box (the throughput workload) in the launch
+    configuration the bench times: one step, every cell against the oracle."""
+    cfg, f = W.spinodal(N=2048)
+    got, ref, dist, st = run_both(S, cfg, f, 1)
+    assert_parity(got, ref, what="2048^2")
+
+
+def test_fp32_shifted_budget(S):
+    """FP32 arithmetic on FP32 deviations from the rest state stays within the
+    phi budget (relative L2 <= 1e-4) of the FP64 oracle on a bubble."""
+    cfg, f = W.stationary_bubble(N=48, R=12.0, rho_ratio=10.0)
+    cfg32 = dict(cfg, precision="fp32", phi_ref=0.5, p_ref=0.0)
+    steps = 400
+    with S.Solver(cfg32, **f) as s:
+        s.step(steps)
+        got = s.macros()
+    o = Oracle(cfg, **f)
+    o.step(steps)
+    ref = o.macros()
+    l2 = np.sqrt(((got["phi"] - ref["phi"]) ** 2).sum() / (ref["phi"] ** 2).sum())
+    assert l2 <= 1e-4, l2
+    assert np.abs(got["p"] - ref["p"]).max() <= 1e-2 * np.abs(ref["p"]).max() + 1e-6
+
+
+def test_fp32_shifted_spinodal_full_size(S):
+    """The bench workload in FP32: one step against the FP64 oracle."""
+    cfg, f = W.spinodal(N=2048)
+    with S.Solver(dict(cfg, precision="fp32"), **f) as s:
+        s.step(1)
+        got = s.macros()
+    o = Oracle(cfg, **f)
+    o.step(1)
+    ref = o.macros()
+    assert np.abs(got["phi"] - ref["phi"]).max() <= 1e-6
+    l2 = np.sqrt(((got["phi"] - ref["phi"]) ** 2).sum() / (ref["phi"] ** 2).sum())
+    assert l2 <= 1e-7, l2
+
+
+def test_reduce_matches_oracle(S):
+    cfg, f = W.random_state(30, 26, seed=9)
+    with S.Solver(cfg, **f) as s:
+        o = Oracle(cfg, **f)
+        for n in (0, 3, 4):
+            s.step(n)
+            o.step(n)
+            g = s.reduce()
+            r = o.reduce()
+            assert g[0] == pytest.approx(r[0], rel=1e-13)
+            assert g[1] == pytest.approx(r[1], rel=1e-6, abs=1e-20)
+            assert g[2] == pytest.approx(r[2], rel=1e-6, abs=1e-20)
+            assert g[3] == pytest.approx(r[3], rel=1e-9)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_restart_bit_identical(S, precision):
+    cfg, f = W.random_state(35, 21, seed=4, bc_y="wall")
+    cfg["precision"] = precision
+    with S.Solver(cfg, **f) as a:
+        a.step(5)
+        ck = a.get_state()
+        a.step(7)
+        want = a.macros()
+        assert a.step_count == 12
+    with S.Solver(cfg, **f) as b:
+        b.set_state(ck)
+        assert b.step_count == 5
+        b.step(7)
+        got = b.macros()
+    for k in want:
+        assert np.array_equal(want[k], got[k]), k
+
+
+def test_nonphysical_state_reported(S):
+    """phi below -1/999 at density ratio 1000 gives rho <= 0: the step records
+    it in the device status word and the next synchronising call reports it."""
+    cfg, f = W.spinodal(N=32)
+    f["phi0"] = np.full((32, 32), -0.01)
+    with S.Solver(cfg, **f) as s:
+        s.step(1)
+        with pytest.raises(S.DugksError) as e:
+            s.sync()
+        assert e.value.code == -5
+
+
+def test_workspace_options_agree(S):
+    """Library-allocated and torch-allocated workspaces give identical results."""
+    cfg, f = W.random_state(21, 19, seed=2)
+    out = []
+    for ws in ("torch", "library"):
+        with S.Solver(cfg, workspace=ws, **f) as s:
+            s.step(4)
+            out.append(s.macros())
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k])
+
+
+def test_zero_steps_is_identity(S):
+    cfg, f = W.random_state(12, 11, seed=8)
+    with S.Solver(cfg, **f) as s:
+        a = s.macros()
+        s.step(0)
+        b = s.macros()
+    for k in a:
+        assert np.array_equal(a[k], b[k])
