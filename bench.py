@@ -1,0 +1,346 @@
+"""Throughput benchmark of the coupled phase-field DUGKS step on GB300.
+
+Workload: the spinodal-decomposition box (Sec. IV.C shape; 2048 x 2048
+periodic cells, density ratio 1000, viscosity ratio 10, sigma = 1e-3, W = 4,
+M = 0.02, phi = 0.5 + 0.01 (2U - 1) from SplitMix64), distributions stored in
+FP32 as deviations from the rest state.  One "step" is one DUGKS time step of
+the whole box (one fused kernel launch).  Metric: million lattice-cell
+updates per second (MLUPS), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (a 2048 x 128 periodic band of the same seeded field) on the host
+cores.  Under torchrun each rank runs an independent replica (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS_SIDE = 2048
+FP32_BYTES_PER_CELL = 18 * 4 * 2 + 2 * 4 * 2   # read + write psi~ (18 FP32) and (phi u) history (2 FP32)
+FP64_BYTES_PER_CELL = 18 * 8 * 2 + 2 * 8 * 2
+REF_BAND_ROWS = 128
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_fp32_spinodal2048.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1810_07802_gb300", "csrc", f)
+                  for f in ("dugks_device.cuh", "dugks_launch.cuh")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload(nx=N_CELLS_SIDE, ny=N_CELLS_SIDE, precision="fp32"):
+    from paper_1810_07802_gb300 import workloads as W
+
+    cfg, f = W.spinodal(N=N_CELLS_SIDE)
+    if ny != N_CELLS_SIDE or nx != N_CELLS_SIDE:
+        f = {k: (None if v is None else v[:ny, :nx].copy()) for k, v in f.items()}
+        cfg.update(nx=nx, ny=ny)
+    cfg["precision"] = precision
+    return cfg, f
+
+
+def config_dict(precision):
+    return {"workload": "spinodal decomposition 2048x2048 periodic, rho ratio 1000, nu ratio 10, "
+                        "sigma 1e-3, W 4, M 0.02, coupled A-C + hydrodynamic D2Q9 DUGKS",
+            "nx": N_CELLS_SIDE, "ny": N_CELLS_SIDE, "precision": precision,
+            "storage": "SoA [18][ny][pitch] deviations from the rest state" if precision == "fp32"
+                       else "SoA [18][ny][pitch] FP64",
+            "l2": "inputs larger than L2 (two 302 MB FP32 state buffers vs 129 MB L2)",
+            "launches_per_step": 1}
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the GPU is busy."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken from the current kernel source; else None."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().lstrip("-* ")
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def time_steps(solver, stream, steps):
+    import torch
+
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    solver.step(steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def run_gpu_measure(precision, steps, warmup, world, rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1810_07802_gb300 import solver as S
+
+    cfg, f = workload(precision=precision)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = S.Solver(cfg, stream=stream, **f)
+    s.step(warmup)
+    s.sync()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    secs = time_steps(s, stream, steps)
+    s.sync()   # raises if the device status word reports a non-finite or non-physical step
+    if world > 1:
+        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    s.close()
+    return secs, cfg
+
+
+def run_e2e(steps, f_host=None):
+    """Same metric through the public API with host buffers: dugks_create from
+    pinned host fields (H2D), K steps, dugks_macros into pinned host arrays
+    (D2H), all inside the timed region."""
+    import numpy as np
+    import torch
+
+    from paper_1810_07802_gb300 import solver as S
+
+    cfg, f = workload(precision="fp32")
+    n = cfg["nx"] * cfg["ny"]
+    pinned = {k: torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float64, pin_memory=True) for k in ("phi0",)}
+    pinned["phi0"].numpy()[:] = f["phi0"]
+    ws = torch.empty(S.workspace_bytes(cfg) + 256, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    ws_view = ws[base - ws.data_ptr():]
+    stream = torch.cuda.Stream()
+    outs = [torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float64, pin_memory=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = S.Solver(cfg, phi0=pinned["phi0"].numpy(), workspace=ws_view, stream=stream)
+    s.step(steps)
+    L = S.lib()
+    ptrs = [o.numpy().ctypes.data_as(S._dp) for o in outs]
+    code = L.dugks_macros(s.h, *ptrs, 0)
+    t1 = time.perf_counter()
+    s.close()
+    if code != 0:
+        raise S.DugksError(code, "dugks_macros")
+    assert np.isfinite(outs[0].numpy()).all()
+    mlups = n * steps / (t1 - t0) / 1e6
+    h2d = n * 8 * 1          # phi0 (ux0, uy0, p0 are zero and not sent)
+    d2h = n * 8 * 4          # phi, p, ux, uy
+    return {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "steps": steps, "region": "dugks_create(host phi0) + dugks_step(K) + dugks_macros(host)"}
+
+
+def cpu_baseline_sample(rows=REF_BAND_ROWS, steps=2):
+    """The FP64 oracle, as it stands, on a 2048 x rows band of the workload."""
+    from oracle.oracle import Oracle
+
+    cfg, f = workload(ny=rows, precision="fp64")
+    o = Oracle(cfg, **f)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return N_CELLS_SIDE * rows * steps / dt / 1e6, dt, cfg
+
+
+def ours(args):
+    import torch
+
+    rank, world, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1810_07802_gb300 import build, solver
+
+    if not os.path.exists(build.LIB_PATH):
+        build.build()
+    solver.lib()
+    dev_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if world == 1 else local
+
+    with ClockSampler(dev_index) as clk:
+        secs, cfg = run_gpu_measure("fp32", args.steps, args.warmup, world, rank)
+    clocks = clk.summary()
+    cells = cfg["nx"] * cfg["ny"]
+    mlups_rank = cells * args.steps / secs / 1e6
+    value = mlups_rank * world
+    ms_step = secs / args.steps * 1e3
+
+    peaks = measured_peaks()
+    peak_gbs, peak_src = (peaks["hbm_gbs"], "measured") if peaks else (6800.0, "fallback")
+    achieved = FP32_BYTES_PER_CELL * cells / (secs / args.steps) / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs, "unit": "GB/s",
+                "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": FP32_BYTES_PER_CELL * cells,
+                "peak_source": peak_src, "kernel": "step_kernel<float,32,8,coupled,periodic>"}
+
+    extra = {}
+    if not args.no_fp64:
+        k64 = max(3, min(args.steps, 40))
+        with ClockSampler(dev_index) as clk64:
+            secs64, _ = run_gpu_measure("fp64", k64, 3, world, rank)
+        ach64 = FP64_BYTES_PER_CELL * cells / (secs64 / k64) / 1e9
+        extra["fp64"] = {"value": round(cells * k64 / secs64 / 1e6 * world, 1), "unit": "MLUPS", "steps": k64,
+                         "ms_per_step": round(secs64 / k64 * 1e3, 4), "hbm_gbs": round(ach64, 1),
+                         "hbm_frac": round(ach64 / peak_gbs, 4), "bound": "fp64 alu",
+                         "clocks": clk64.summary()}
+
+    line = {"metric": "coupled DUGKS MLUPS (spinodal 2048^2, FP32-shifted)", "value": round(value, 1),
+            "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64 spinodal field)",
+            "config": dict(config_dict("fp32"), parallelism="replicas" if world > 1 else "single GPU"),
+            "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps}
+    if rank == 0:
+        line["e2e"] = run_e2e(args.steps)
+        if not args.no_cpu_baseline:
+            v, dt, _ = cpu_baseline_sample()
+            line["cpu_baseline"] = {"value": round(v, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                    "sample": "2 FP64 steps of a 2048x%d periodic band of the same seeded field "
+                                              "(%.1f s, single-threaded C oracle)" % (REF_BAND_ROWS, dt)}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference(args):
+    rank, world, _ = dist_setup(args)
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline_sample(rows=8, steps=1)
+    total_cells = 0
+    t_total = 0.0
+    for _ in range(args.steps):
+        v, dt, cfg = cpu_baseline_sample(rows=REF_BAND_ROWS // 4, steps=1)
+        total_cells += cfg["nx"] * cfg["ny"]
+        t_total += dt
+    value = total_cells / t_total / 1e6
+    line = {"metric": "coupled DUGKS MLUPS (spinodal 2048^2, FP32-shifted)", "value": round(value, 4),
+            "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_total / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded SplitMix64 spinodal field)",
+            "config": config_dict("fp64"), "impl": "reference",
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "each step: 1 FP64 step of a 2048x%d periodic band of the workload "
+                                       "on the host (single-threaded C oracle)" % (REF_BAND_ROWS // 4)},
+            "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference(a)
+    else:
+        ours(a)

@@ -26,7 +26,10 @@
  *      = [4 (E+W+N+S) + (NE+NW+SE+SW) - 20 C] / 6.
  *  R5  d_t(phi u) in Eq. 16 by the explicit difference
  *      ((phi u)^n - (phi u)^{n-1}) / dt, and 0 on the first step.
- *  R6  n = grad phi / |grad phi| when |grad phi|^2 > 1e-28, else n = 0.
+ *  R6  n = grad phi / sqrt(|grad phi|^2 + 1e-16): the unit normal wherever an
+ *      interface is resolved (|grad phi| >> 1e-8), and a continuous function
+ *      of grad phi where it vanishes, so that round-off in a flat region
+ *      cannot flip n between 0 and a unit vector.
  *  R7  Initial state psi~ = psi_eq - dt/2 S (Eq. 23a with psi = psi_eq) and
  *      d_t(phi u) = 0; (phi u)^{-1} = phi0 u0.
  *  R8  Gravity G = (gx, gy), or (rho - rho_ref)(gx, gy).
@@ -201,15 +204,9 @@ static void closures(const oracle_params *P, point_state *s)
 {
     double phi = s->phi;
     s->theta = -4.0 * (phi - 1.0) * (phi - 0.0) / (P->width * (1.0 - 0.0));   /* Eq. 6 */
-    double g2 = s->dphix * s->dphix + s->dphiy * s->dphiy;
-    if (g2 > 1e-28) {
-        double gn = sqrt(g2);
-        s->nx = s->dphix / gn;
-        s->ny = s->dphiy / gn;
-    } else {
-        s->nx = 0.0;
-        s->ny = 0.0;
-    }
+    double gn = sqrt(s->dphix * s->dphix + s->dphiy * s->dphiy + 1e-16);   /* R6 */
+    s->nx = s->dphix / gn;
+    s->ny = s->dphiy / gn;
     if (P->model != 0) return;   /* A-C only: no hydrodynamics */
 
     double beta = 12.0 * P->sigma / P->width;     /* Eq. 3 */

@@ -14,7 +14,8 @@
 //   * Isotropic D2Q9 gradient (1/RT) sum_i w_i xi_i phi(x + xi_i) and the
 //     nine-point Laplacian [4(E+W+N+S) + (NE+NW+SE+SW) - 20 C] / 6.
 //   * d_t(phi u) = ((phi u)^n - (phi u)^{n-1}) / dt, zero on the first step.
-//   * n = grad phi / |grad phi| if |grad phi|^2 > 1e-28, else 0.
+//   * n = grad phi / sqrt(|grad phi|^2 + 1e-16): the unit normal wherever an
+//     interface is resolved, continuous where grad phi vanishes.
 //   * No-slip walls on y = 0 and y = ny: phi mirrored into ghost rows;
 //     one-sided y-slope for x-faces of the first/last row; at a wall face,
 //     directions leaving the fluid or running along the wall are extrapolated
@@ -104,15 +105,9 @@ template <typename Real, bool COUPLED>
 __device__ __forceinline__ void closures(const Phys<Real> &ph, Pt<Real> &s) {
     const Real phi = s.phi;
     s.theta = ph.theta_k * phi * (Real(1) - phi);
-    const Real g2 = s.dpx * s.dpx + s.dpy * s.dpy;
-    if (g2 > Real(1e-28)) {
-        const Real inv = rsqrt_r(g2);
-        s.nx = s.dpx * inv;
-        s.ny = s.dpy * inv;
-    } else {
-        s.nx = Real(0);
-        s.ny = Real(0);
-    }
+    const Real inv = rsqrt_r(s.dpx * s.dpx + s.dpy * s.dpy + Real(1e-16));
+    s.nx = s.dpx * inv;
+    s.ny = s.dpy * inv;
     if (COUPLED) {
         s.rho = ph.rho_l + ph.drho * phi;
         s.drx = ph.drho * s.dpx;
