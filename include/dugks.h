@@ -146,6 +146,31 @@ dugks_status dugks_sync(dugks_handle h);
 /* Frees the handle and the memory the library allocated.  Synchronises. */
 dugks_status dugks_destroy(dugks_handle h);
 
+/* Allocation-free FP64 reduction of macro fields (the paper has no
+ * counterpart; this is a convenience for callers that cannot allocate).
+ * Some callers cannot call cudaMalloc/cudaFree where they need a convergence
+ * check: code being recorded into a CUDA graph (allocation is illegal while a
+ * stream is captured), serving loops that plan all device memory up front,
+ * or hosts without an allocator of their own.  This call takes device arrays
+ * phi, ux, uy of n doubles (for example dugks_macros output with
+ * dst_is_device = 1) and, optionally, snap = [3][n] doubles (phi, ux, uy of an
+ * earlier time; NULL if none), and writes four doubles to the device array
+ * out: the phi mass sum(phi), the residuals of Eq. 44 for phi and for u
+ * against snap (1.0 when snap is NULL), and max |u|.  It is enqueued on
+ * cuda_stream (cudaStream_t or NULL) and does not synchronise.
+ * It allocates nothing: its per-block partial sums live in a fixed device
+ * array inside this library (192 KiB, present on every GPU that loads the
+ * library until the process exits), which bounds n to
+ * DUGKS_STATIC_REDUCE_MAX_CELLS; larger n, n < 1 or a NULL phi/ux/uy/out
+ * return DUGKS_ERR_ARG without launching anything.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Every call shares the array: calls that can overlap on the GPU (other
+ * streams or host threads) race and must be serialised by the caller. */
+#define DUGKS_STATIC_REDUCE_MAX_CELLS 16777216
+dugks_status dugks_reduce_fields_static(const double *phi, const double *ux, const double *uy,
+                                        const double *snap, int64_t n, double *out, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *dugks_status_string(dugks_status s);
 

@@ -51,7 +51,10 @@ SIGNATURES = {
     "dugks_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "dugks_reduce_fields_static": (ctypes.c_int, [_dp, _dp, _dp, _dp, ctypes.c_int64, _dp, ctypes.c_void_p]),
 }
+
+STATIC_REDUCE_MAX_CELLS = 16777216
 
 
 class DugksError(RuntimeError):
@@ -133,6 +136,24 @@ def _host(a, shape):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(_dp)
+
+
+def reduce_fields_static(phi, ux, uy, out, snap=None, stream=None):
+    """dugks_reduce_fields_static on CUDA float64 tensors (no allocation in the
+    library): phi, ux, uy of n elements, snap of 3n or None, out of 4 elements
+    receives (phi mass, residual of phi, residual of u, max |u|)."""
+    import torch
+
+    n = phi.numel()
+    if n > STATIC_REDUCE_MAX_CELLS:
+        raise ValueError("dugks_reduce_fields_static takes at most %d cells, got %d" % (STATIC_REDUCE_MAX_CELLS, n))
+    st = stream if stream is not None else torch.cuda.current_stream()
+
+    def p(t):
+        return None if t is None else ctypes.cast(t.data_ptr(), _dp)
+
+    code = lib().dugks_reduce_fields_static(p(phi), p(ux), p(uy), p(snap), n, p(out), ctypes.c_void_p(st.cuda_stream))
+    _check(code, "dugks_reduce_fields_static")
 
 
 class Solver:
