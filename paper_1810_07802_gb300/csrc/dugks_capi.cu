@@ -6,6 +6,9 @@
 #include <cstring>
 #include <new>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "dugks.h"
 #include "dugks_aux.cuh"
 #include "dugks_internal.h"
@@ -95,6 +98,7 @@ Phys<Real> make_phys(const dugks_params &p) {
     ph.h = Real(h);
     ph.half_dt = Real(0.5 * dt);
     ph.half_h = Real(0.5 * h);
+    ph.inv_dt = Real(1.0 / dt);
     ph.pf_a = Real((2 * tau - h) / (2 * tau + dt));  // Eq. 29
     ph.pf_b = Real(3 * h / (2 * tau + dt));
     ph.pf_c = Real(3 * tau * h / (2 * tau + dt));
@@ -132,6 +136,37 @@ dugks_status from_cuda(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? DUGKS_ERR_OOM : DUGKS_ERR_CUDA;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// 3-D map over [planes][ny][pitch] (extent nx in x) with a box of
+// (box_x, box_y, planes) elements.  Returns false if unavailable.
+bool make_box_map(CUtensorMap *m, void *base, bool f64, int nx, int ny, int pitch, int planes, int box_x, int box_y) {
+    std::memset(m, 0, sizeof *m);
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || box_x > 256 || box_y > 256 || planes > 256) return false;
+    const size_t elt = f64 ? 8 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * elt, (cuuint64_t)pitch * elt * (cuuint64_t)ny};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)planes};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 struct dugks_ctx {
@@ -147,6 +182,8 @@ struct dugks_ctx {
     unsigned status_seen;
     Phys<double> phd;
     Phys<float> phf;
+    bool tma_ok;
+    CUtensorMap tm_state[2], tm_hist[2];
 
     void *state(int b) const { return ws + L.off_state[b]; }
     void *hist(int b) const { return ws + L.off_hist[b]; }
@@ -179,6 +216,7 @@ dugks_status sync_status(dugks_ctx *c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return from_cuda(e);
     c->status_seen |= s;
+    if (c->status_seen & dugks::STATUS_TIMEOUT) return DUGKS_ERR_TIMEOUT;
     if (c->status_seen & dugks::STATUS_NONFINITE) return DUGKS_ERR_NONFINITE;
     if (c->status_seen & dugks::STATUS_NONPHYSICAL) return DUGKS_ERR_NONPHYSICAL;
     return DUGKS_OK;
@@ -240,6 +278,17 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
         c->owns = true;
     }
 
+    {
+        const int tx = c->fp32 ? dugks::step_tile<float>(0) : dugks::step_tile<double>(0);
+        const int ty = c->fp32 ? dugks::step_tile<float>(1) : dugks::step_tile<double>(1);
+        c->tma_ok = true;
+        for (int b = 0; b < 2; b++) {
+            c->tma_ok = c->tma_ok && make_box_map(&c->tm_state[b], c->state(b), !c->fp32, params->nx, params->ny,
+                                                  L.pitch, L.nq, tx + 8, ty + 4);
+            c->tma_ok = c->tma_ok && make_box_map(&c->tm_hist[b], c->hist(b), !c->fp32, params->nx, params->ny,
+                                                  L.pitch, 2, tx + 8, ty + 4);
+        }
+    }
     cudaError_t e = cudaMemsetAsync(c->ws, 0, L.off_stage, c->st);  // state, history (incl. row padding)
     const size_t fb = L.n * sizeof(double);
     double *in = c->stage();
@@ -287,8 +336,11 @@ dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
             a.pitch = c->L.pitch;
             a.plane = (long long)c->L.plane;
             a.first_step = c->steps == 0;
+            a.small = 1;
+            a.use_tma = c->tma_ok;
             a.status = c->status();
-            e = dugks::launch_step<float>(a, c->phf, c->coupled, c->wally, c->st);
+            e = dugks::launch_step<float>(a, c->phf, c->coupled, c->wally, &c->tm_state[c->cur], &c->tm_hist[c->cur],
+                                          c->st);
         } else {
             StepArgs<double> a;
             a.src = static_cast<const double *>(c->state(c->cur));
@@ -300,8 +352,11 @@ dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
             a.pitch = c->L.pitch;
             a.plane = (long long)c->L.plane;
             a.first_step = c->steps == 0;
+            a.small = 1;
+            a.use_tma = c->tma_ok;
             a.status = c->status();
-            e = dugks::launch_step<double>(a, c->phd, c->coupled, c->wally, c->st);
+            e = dugks::launch_step<double>(a, c->phd, c->coupled, c->wally, &c->tm_state[c->cur],
+                                           &c->tm_hist[c->cur], c->st);
         }
         if (e != cudaSuccess) return from_cuda(e);
         c->cur = nxt;

@@ -30,6 +30,7 @@
 // only where the closures need absolute values.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,12 +56,29 @@ __host__ __device__ constexpr int yslot(int k) {
     return k == 2 ? 0 : k == 3 ? 1 : k == 4 ? 2 : k == 6 ? 3 : k == 7 ? 4 : k == 8 ? 5 : -1;
 }
 
-enum : unsigned { STATUS_NONFINITE = 1u, STATUS_NONPHYSICAL = 2u };
+// a * x for a in {-1, 0, 1}.  IEEE rules forbid the compiler from folding
+// 0 * x or 0 - x, so every product with a lattice-velocity component is
+// written out case by case (k is a compile-time constant after unrolling).
+template <typename Real>
+__device__ __forceinline__ Real sgnmul(int a, Real x) { return a > 0 ? x : -x; }
+// xi_k . (x, y) for k != 0.
+template <typename Real>
+__device__ __forceinline__ Real edot(int k, Real x, Real y) {
+    const int a = cx(k), b = cy(k);
+    if (a == 0) return sgnmul(b, y);
+    if (b == 0) return sgnmul(a, x);
+    return b > 0 ? sgnmul(a, x) + y : sgnmul(a, x) - y;
+}
+// xi_k,a - u for a component a in {-1, 0, 1}.
+template <typename Real>
+__device__ __forceinline__ Real eminus(int a, Real u) { return a == 0 ? -u : (a > 0 ? Real(1) - u : Real(-1) - u); }
+
+enum : unsigned { STATUS_NONFINITE = 1u, STATUS_NONPHYSICAL = 2u, STATUS_TIMEOUT = 4u };
 
 // Constants of one problem, computed once on the host (passed by value).
 template <typename Real>
 struct Phys {
-    Real dt, h, half_dt, half_h;
+    Real dt, h, half_dt, half_h, inv_dt;
     Real pf_a, pf_b, pf_c;      // Eq. 29 coefficients for f (tau_f constant)
     Real ff_a, ff_b, ff_c;      // Eq. 28 coefficients for f
     Real beta4, kappa, theta_k; // 4 beta, kappa (Eq. 3), 4 / W (Eq. 6)
@@ -81,6 +99,8 @@ struct StepArgs {
     int nx, ny, pitch;
     long long plane;               // ny * pitch
     int first_step;
+    int small;                     // grid smaller than a tile plus halo: wrap with %
+    int use_tma;                   // tensor maps are valid: interior tiles load by TMA
     unsigned *status;
 };
 
@@ -88,7 +108,7 @@ struct StepArgs {
 template <typename Real>
 struct Pt {
     Real phi, dpx, dpy, lap;
-    Real rho, drx, dry, taug;
+    Real rho, irho, drx, dry, taug;
     Real theta, nx, ny;
     Real Fx, Fy, ux, uy, pd;  // pd = p - p_ref
     Real Dx, Dy;
@@ -96,6 +116,10 @@ struct Pt {
 
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+// Reciprocal: the FP32 path uses the fast hardware reciprocal (a few ulp),
+// the FP64 path IEEE division.
+__device__ __forceinline__ float rcp_r(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
 __device__ __forceinline__ bool finite_r(float x) { return isfinite(x); }
 __device__ __forceinline__ bool finite_r(double x) { return isfinite(x); }
 
@@ -114,8 +138,9 @@ __device__ __forceinline__ void closures(const Phys<Real> &ph, Pt<Real> &s) {
         s.dry = ph.drho * s.dpy;
         const Real muphi = ph.beta4 * phi * (phi - Real(1)) * (phi - Real(0.5)) - ph.kappa * s.lap;
         const Real lin = ph.visc_a * phi + ph.visc_b;
-        const Real mu = ph.visc_linear ? lin : Real(1) / lin;
-        s.taug = Real(3) * mu / s.rho;
+        const Real mu = ph.visc_linear ? lin : rcp_r(lin);
+        s.irho = rcp_r(s.rho);
+        s.taug = Real(3) * mu * s.irho;
         Real Gx = ph.gx, Gy = ph.gy;
         if (ph.grav_mode) {
             Gx = (s.rho - ph.rho_ref) * ph.gx;
@@ -129,9 +154,8 @@ __device__ __forceinline__ void closures(const Phys<Real> &ph, Pt<Real> &s) {
 // u and p' from the g moments (Eqs. 32-33; half = dt/2 at a cell, h/2 at a face).
 template <typename Real>
 __device__ __forceinline__ void velocity_pressure(Real mx, Real my, Real sn, Real half, Pt<Real> &s) {
-    const Real irho = Real(1) / s.rho;
-    s.ux = (mx + half * s.Fx) * irho;
-    s.uy = (my + half * s.Fy) * irho;
+    s.ux = (mx + half * s.Fx) * s.irho;
+    s.uy = (my + half * s.Fy) * s.irho;
     // RT/(1 - w0) = 3/5; rho (Gamma_0(u) - Gamma_0(0)) = -(2/3) rho |u|^2
     s.pd = Real(0.6) * (sn + half * (s.ux * s.drx + s.uy * s.dry)
                         - Real(2) / Real(3) * s.rho * (s.ux * s.ux + s.uy * s.uy));
@@ -141,117 +165,313 @@ __device__ __forceinline__ void velocity_pressure(Real mx, Real my, Real sn, Rea
 template <typename Real>
 __device__ __forceinline__ void f_eq_src(int k, const Phys<Real> &ph, const Pt<Real> &s, Real &eq, Real &src) {
     const Real w = wq<Real>(k);
-    const Real ex = Real(cx(k)), ey = Real(cy(k));
-    const Real eu = ex * s.ux + ey * s.uy;
+    if (k == 0) {
+        eq = w * (s.phi - ph.phi_ref);
+        src = Real(0);
+        return;
+    }
+    const Real eu = edot(k, s.ux, s.uy);
     eq = w * ((s.phi - ph.phi_ref) + Real(3) * s.phi * eu);
-    src = w * (s.theta * (ex * s.nx + ey * s.ny) + Real(3) * (ex * s.Dx + ey * s.Dy));
+    src = w * (s.theta * edot(k, s.nx, s.ny) + Real(3) * edot(k, s.Dx, s.Dy));
 }
 
 // Deviation of g_eq (Eqs. 17-18) and S^g (Eq. 19) in direction k.
 template <typename Real>
 __device__ __forceinline__ void g_eq_src(int k, const Pt<Real> &s, Real &eq, Real &src) {
     const Real w = wq<Real>(k);
-    const Real ex = Real(cx(k)), ey = Real(cy(k));
-    const Real eu = ex * s.ux + ey * s.uy;
     const Real usq = s.ux * s.ux + s.uy * s.uy;
-    const Real gam = w * (Real(3) * eu + Real(4.5) * eu * eu - Real(1.5) * usq);  // Gamma_k(u) - w_k
-    eq = Real(3) * s.pd * (k == 0 ? w - Real(1) : w) + s.rho * gam;
+    Real gam;  // Gamma_k(u) - w_k
+    if (k == 0) {
+        gam = w * (Real(-1.5) * usq);
+        eq = Real(3) * s.pd * (w - Real(1)) + s.rho * gam;
+    } else {
+        const Real eu = edot(k, s.ux, s.uy);
+        gam = w * (eu * (Real(3) + Real(4.5) * eu) - Real(1.5) * usq);
+        eq = Real(3) * s.pd * w + s.rho * gam;
+    }
     const Real G = w + gam;
-    src = (ex - s.ux) * (gam * s.drx + Real(3) * s.Fx * G) + (ey - s.uy) * (gam * s.dry + Real(3) * s.Fy * G);
+    const Real A = gam * s.drx + Real(3) * s.Fx * G;
+    const Real B = gam * s.dry + Real(3) * s.Fy * G;
+    src = eminus(cx(k), s.ux) * A + eminus(cy(k), s.uy) * B;
 }
 
 __device__ __forceinline__ int wrap(int x, int n) {
     x %= n;
     return x < 0 ? x + n : x;
 }
+// Periodic index for x in [-n, 2n) (one correction either way).
+__device__ __forceinline__ int wrap1(int x, int n) {
+    x += (x < 0) ? n : 0;
+    return x - ((x >= n) ? n : 0);
+}
 // Row index for phi stencils: periodic, or mirrored at the walls (rows far
 // outside are clamped; no valid cell's stencil reaches them).
 template <bool WALLY>
-__device__ __forceinline__ int map_row(int y, int ny) {
-    if (!WALLY) return wrap(y, ny);
+__device__ __forceinline__ int map_row(int y, int ny, bool small = true) {
+    if (!WALLY) return small ? wrap(y, ny) : wrap1(y, ny);
     if (y < 0) y = -1 - y;
     if (y >= ny) y = 2 * ny - 1 - y;
     return y < 0 ? 0 : (y >= ny ? ny - 1 : y);
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory records.
+//
+// psi-bar-plus of one cell is a record of slots grouped by lattice direction,
+// so that a face reads only the groups it needs, 16 bytes at a time:
+//   coupled:  [f2 f4 f6 f8] [g2 g4 g6 g8] [f1 f5 g1 g5] [f3 f7 g3 g7] [f0 g0 - -]
+//   A-C only: [f2 f4 f6 f8] [f1 f5 f3 f7] [f0 - - -]
+// The diagonal groups need tangential neighbours at every face, the axis
+// groups only at the faces they run along.  Record strides are chosen so that
+// eight consecutive cells fall in distinct banks for 16-byte accesses.
+template <bool COUPLED> struct Rec;
+template <> struct Rec<true> {
+    static constexpr int NG = 5;
+    __host__ __device__ static constexpr int model(int s) {
+        return s < 4 ? 0 : s < 8 ? 1 : s < 16 ? ((s & 2) ? 1 : 0) : (s == 16 ? 0 : 1);
+    }
+    __host__ __device__ static constexpr int dir(int s) {
+        return s < 8 ? 2 + 2 * (s & 3) : s < 12 ? ((s & 1) ? 5 : 1) : s < 16 ? ((s & 1) ? 7 : 3) : 0;
+    }
+    __host__ __device__ static constexpr bool used(int s) { return s < 18; }
+    __host__ __device__ static constexpr int slot(int m, int k) {
+        return k == 0 ? 16 + m : (k & 1) == 0 ? 4 * m + (k - 2) / 2 : (k == 1 || k == 5) ? 8 + 2 * m + (k == 5) : 12 + 2 * m + (k == 7);
+    }
+};
+template <> struct Rec<false> {
+    static constexpr int NG = 3;
+    __host__ __device__ static constexpr int model(int) { return 0; }
+    __host__ __device__ static constexpr int dir(int s) {
+        return s < 4 ? 2 + 2 * s : s == 4 ? 1 : s == 5 ? 5 : s == 6 ? 3 : s == 7 ? 7 : 0;
+    }
+    __host__ __device__ static constexpr bool used(int s) { return s < 9; }
+    __host__ __device__ static constexpr int slot(int, int k) {
+        return k == 0 ? 8 : (k & 1) == 0 ? (k - 2) / 2 : k == 1 ? 4 : k == 5 ? 5 : k == 3 ? 6 : 7;
+    }
+};
+
+// Does group G hold a direction whose tangential slope is needed at an
+// x-face (xi_y != 0) or a y-face (xi_x != 0)?
+template <bool COUPLED, bool XFACE>
+__host__ __device__ constexpr bool group_tangential(int G) {
+    bool any = false;
+    for (int j = 0; j < 4; j++) {
+        const int s = 4 * G + j;
+        if (Rec<COUPLED>::used(s)) {
+            const int k = Rec<COUPLED>::dir(s);
+            any = any || (XFACE ? cy(k) != 0 : cx(k) != 0);
+        }
+    }
+    return any;
+}
+
+// 16-byte aligned groups of four values.
+__device__ __forceinline__ void ld4(const float *p, float o[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double o[4]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double *p, double a, double b, double c, double d) {
+    *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(c, d);
+}
+// Pairs (8-byte aligned for float, 16-byte for double).
+__device__ __forceinline__ void ld2(const float *p, float o[2]) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    o[0] = v.x; o[1] = v.y;
+}
+__device__ __forceinline__ void ld2(const double *p, double o[2]) {
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    o[0] = v.x; o[1] = v.y;
+}
+__device__ __forceinline__ void st2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st2(double *p, double a, double b) { *reinterpret_cast<double2 *>(p) = make_double2(a, b); }
+
 template <typename Real, int TX, int TY, bool COUPLED>
 struct TileShape {
+    static constexpr bool F64 = sizeof(Real) == 8;
     static constexpr int NT = TX * TY;
     static constexpr int HX2 = TX + 4, HY2 = TY + 4;  // phi region (halo 2)
     static constexpr int HX1 = TX + 2, HY1 = TY + 2;  // psi-bar-plus region (halo 1)
     static constexpr int N2 = HX2 * HY2, N1 = HX1 * HY1;
     static constexpr int NQ = COUPLED ? 18 : 9;
+    // Input box: columns x0-4 .. x0+TX+3 (the left edge rounded down to a
+    // 16-byte boundary for TMA), rows y0-2 .. y0+TY+1, the NQ distribution
+    // planes followed by the 2 history planes.
+    static constexpr int BX = TX + 8, BY = TY + 4, BXY = BX * BY;
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-    static constexpr int NFD = COUPLED ? 12 : 6;  // flux slots per face
-    static constexpr size_t off_phi = 0;
-    static constexpr size_t off_bp = off_phi + N2;
-    static constexpr size_t off_aux = off_bp + size_t(NQ) * N1;
-    static constexpr size_t off_fx = off_aux + size_t(5) * N1;
-    static constexpr size_t off_fy = off_fx + size_t(NFD) * NFX;
-    static constexpr size_t smem_elems = off_fy + size_t(NFD) * NFY;
-    static constexpr size_t smem_bytes = smem_elems * sizeof(Real);
+    static constexpr int NFD = COUPLED ? 12 : 6;                               // flux values per face
+    static constexpr int RS = Rec<COUPLED>::NG * 4 + (F64 ? 2 : 0);            // record stride
+    static constexpr int AS = F64 ? 6 : 4;                                     // aux stride (FP32: d_t(phi u)_y apart)
+    static constexpr int FS = COUPLED ? (F64 ? 14 : 12) : 6;                   // flux record stride
+    static constexpr int AL = 128 / int(sizeof(Real));                         // 128-byte alignment
+    static constexpr size_t up(size_t v) { return (v + AL - 1) / AL * AL; }
+    static constexpr size_t off_box = 0;
+    static constexpr size_t off_hbox = off_box + size_t(NQ) * BXY;
+    static constexpr size_t off_phi = up(off_hbox + size_t(2) * BXY);
+    static constexpr size_t off_rec = up(off_phi + N2);
+    static constexpr size_t off_aux = up(off_rec + size_t(RS) * N1);
+    static constexpr size_t off_dy = up(off_aux + size_t(AS) * N1);
+    static constexpr size_t off_bar = up(off_dy + (F64 ? 0 : size_t(N1)));  // mbarrier, then a flag
+    static constexpr size_t smem_elems = off_bar + 16 / sizeof(Real);
+    static constexpr size_t smem_bytes = smem_elems * sizeof(Real) + 128;    // + room to align the base
+    // The face fluxes reuse the input box once phase 2 has consumed it.
+    static constexpr size_t off_fx = off_box;
+    static constexpr size_t off_fy = off_fx + (size_t(FS) * NFX + 3) / 4 * 4;
+    static_assert(off_fy + size_t(FS) * NFY <= off_phi, "face fluxes must fit in the input box");
+    static_assert((size_t(NQ) * BXY * sizeof(Real)) % 128 == 0, "TMA destinations must be 128-byte aligned");
+    static_assert((BX * sizeof(Real)) % 16 == 0, "TMA box rows must be multiples of 16 bytes");
 };
 
-// Central reconstruction (Eq. 27) of the 9 directions of one model whose
-// psi-bar-plus planes are b[k * N1 + cell], at the face between cells L and
-// R = L + nstride.  The tangential slope uses rows L +- tstride: tmode 0
-// central, +1 one-sided towards +t, -1 one-sided towards -t.
-template <typename Real, bool XFACE>
-__device__ __forceinline__ void recon9(const Real *__restrict__ b, int N1, int L, int R, int tstride,
-                                       int tmode, Real h, Real out[9]) {
+// ---- TMA (cp.async.bulk.tensor) and mbarrier helpers ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+#ifdef __CUDA_ARCH__
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+#else
+    return 0;
+#endif
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+#ifdef __CUDA_ARCH__
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+#ifdef __CUDA_ARCH__
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+#endif
+}
+// 3-D tiled TMA load of the box at (x, y, z) into shared memory.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+#ifdef __CUDA_ARCH__
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+#endif
+}
+// Waits for phase `parity` of the barrier, at most max_polls polls.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long max_polls) {
+#ifdef __CUDA_ARCH__
+    for (long i = 0; i < max_polls; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+#else
+    return true;
+#endif
+}
+
+// Central reconstruction (Eq. 27) at the face between cells A and B (record
+// indices) of every direction needed there.  The tangential slope uses the
+// records at A +- tstride, B +- tstride: tmode 0 central, +1 one-sided
+// towards +t, -1 one-sided towards -t.  The rest direction of g is not needed
+// by any face quantity and is skipped.
+template <typename Real, bool COUPLED, bool XFACE, int RS>
+__device__ __forceinline__ void recon_face(const Real *__restrict__ rec, int A, int B, int tstride, int tmode, Real h,
+                                           Real fb[9], Real gb[9]) {
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
-        const Real *p = b + k * N1;
-        const Real A = p[L], B = p[R];
-        Real st;
-        if (tmode == 0)
-            st = Real(0.25) * ((p[L + tstride] - p[L - tstride]) + (p[R + tstride] - p[R - tstride]));
-        else if (tmode > 0)
-            st = Real(0.5) * ((p[L + tstride] - A) + (p[R + tstride] - B));
-        else
-            st = Real(0.5) * ((A - p[L - tstride]) + (B - p[R - tstride]));
-        const Real sn = B - A;
-        const Real cn = Real(XFACE ? cx(k) : cy(k)), ct = Real(XFACE ? cy(k) : cx(k));
-        out[k] = Real(0.5) * (A + B) - h * (cn * sn + ct * st);
+    for (int G = 0; G < Rec<COUPLED>::NG; G++) {
+        Real a[4], b[4], an[4], as[4], bn[4], bs[4];
+        ld4(rec + A * RS + 4 * G, a);
+        ld4(rec + B * RS + 4 * G, b);
+        const bool tang = group_tangential<COUPLED, XFACE>(G);
+        if (tang) {
+            if (tmode >= 0) {
+                ld4(rec + (A + tstride) * RS + 4 * G, an);
+                ld4(rec + (B + tstride) * RS + 4 * G, bn);
+            }
+            if (tmode <= 0) {
+                ld4(rec + (A - tstride) * RS + 4 * G, as);
+                ld4(rec + (B - tstride) * RS + 4 * G, bs);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int s = 4 * G + j;
+            if (!Rec<COUPLED>::used(s)) continue;
+            const int k = Rec<COUPLED>::dir(s), m = Rec<COUPLED>::model(s);
+            if (m == 1 && k == 0) continue;
+            const int cn = XFACE ? cx(k) : cy(k), ct = XFACE ? cy(k) : cx(k);
+            Real v = Real(0.5) * (a[j] + b[j]);
+            if (cn != 0) v -= h * sgnmul(cn, b[j] - a[j]);
+            if (ct != 0) {
+                Real st;
+                if (tmode == 0)
+                    st = Real(0.25) * ((an[j] - as[j]) + (bn[j] - bs[j]));
+                else if (tmode > 0)
+                    st = Real(0.5) * ((an[j] - a[j]) + (bn[j] - b[j]));
+                else
+                    st = Real(0.5) * ((a[j] - as[j]) + (b[j] - bs[j]));
+                v -= h * sgnmul(ct, st);
+            }
+            if (m == 0) fb[k] = v; else gb[k] = v;
+        }
     }
 }
 
 // Wall face, bottom (TOP == false) or top: linear extrapolation from cell c0
 // (next cell into the fluid at c0 + inward) for directions leaving the fluid
 // or tangential, bounce-back for directions entering it.
-template <typename Real, bool TOP>
-__device__ __forceinline__ void recon_wall9(const Real *__restrict__ b, int N1, int c0, int inward, Real h,
-                                            Real out[9]) {
+template <typename Real, bool COUPLED, bool TOP, int RS>
+__device__ __forceinline__ void recon_wall(const Real *__restrict__ rec, int c0, int inward, Real h, Real fb[9],
+                                           Real gb[9]) {
     const Real dyw = TOP ? Real(0.5) : Real(-0.5);
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
-        const bool keep = TOP ? (cy(k) >= 0) : (cy(k) <= 0);
-        if (keep) {
-            const Real *p = b + k * N1;
-            const Real b0 = p[c0];
-            const Real sx = Real(0.5) * (p[c0 + 1] - p[c0 - 1]);
-            const Real sy = TOP ? (b0 - p[c0 + inward]) : (p[c0 + inward] - b0);
-            out[k] = b0 + (-h * Real(cx(k))) * sx + (dyw - h * Real(cy(k))) * sy;
+    for (int m = 0; m < (COUPLED ? 2 : 1); m++) {
+        Real *out = m == 0 ? fb : gb;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const bool keep = TOP ? (cy(k) >= 0) : (cy(k) <= 0);
+            if (!keep) continue;
+            const int sl = Rec<COUPLED>::slot(m, k);
+            const Real b0 = rec[c0 * RS + sl];
+            const Real sy = TOP ? (b0 - rec[(c0 + inward) * RS + sl]) : (rec[(c0 + inward) * RS + sl] - b0);
+            Real v = b0 + (cy(k) == 0 ? dyw : (cy(k) > 0 ? dyw - h : dyw + h)) * sy;
+            if (cx(k) != 0) v -= h * sgnmul(cx(k), Real(0.5) * (rec[(c0 + 1) * RS + sl] - rec[(c0 - 1) * RS + sl]));
+            out[k] = v;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const bool enters = TOP ? (cy(k) < 0) : (cy(k) > 0);
+            if (enters) out[k] = out[opp(k)];
         }
     }
-#pragma unroll
-    for (int k = 0; k < 9; k++) {
-        const bool enters = TOP ? (cy(k) < 0) : (cy(k) > 0);
-        if (enters) out[k] = out[opp(k)];
-    }
+}
+
+// First moments and non-rest sum of the g distributions (Eqs. 32-33).
+template <typename Real>
+__device__ __forceinline__ void moments9(const Real g[9], Real &mx, Real &my, Real &sn) {
+    // directions 1..8: (1,0) (1,1) (0,1) (-1,1) (-1,0) (-1,-1) (0,-1) (1,-1)
+    mx = ((g[1] + g[2]) + g[8]) - ((g[4] + g[5]) + g[6]);
+    my = ((g[2] + g[3]) + g[4]) - ((g[6] + g[7]) + g[8]);
+    sn = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
 }
 
 // Face state from f_bar, g_bar and the face values of the aux fields, then
 // the original distributions (Eq. 28) of the directions crossing the face,
-// written to out[slot * stride] (f slots 0..5, g slots 6..11).
+// in flux-slot order: out[slot] for f, out[6 + slot] for g.
 template <typename Real, bool COUPLED, bool XFACE>
 __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9], const Real gb[9], Real dpx,
-                                          Real dpy, Real lap, Real Dx, Real Dy, bool wall, Real *__restrict__ out,
-                                          int stride) {
+                                          Real dpy, Real lap, Real Dx, Real Dy, bool wall, Real out[12]) {
     Pt<Real> s;
-    Real sphi = Real(0);
+    Real sphi = fb[0];
 #pragma unroll
-    for (int k = 0; k < 9; k++) sphi += fb[k];
+    for (int k = 1; k < 9; k++) sphi += fb[k];
     s.phi = ph.phi_ref + sphi;
     s.dpx = dpx;
     s.dpy = dpy;
@@ -260,13 +480,8 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
     s.Dy = Dy;
     closures<Real, COUPLED>(ph, s);
     if (COUPLED) {
-        Real mx = Real(0), my = Real(0), sn = Real(0);
-#pragma unroll
-        for (int k = 0; k < 9; k++) {
-            mx += Real(cx(k)) * gb[k];
-            my += Real(cy(k)) * gb[k];
-            if (k) sn += gb[k];
-        }
+        Real mx, my, sn;
+        moments9(gb, mx, my, sn);
         if (wall) {
             s.ux = Real(0);
             s.uy = Real(0);
@@ -279,26 +494,51 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
         s.uy = wall ? Real(0) : ph.u0y;
     }
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
+    for (int k = 1; k < 9; k++) {
         const int slot = XFACE ? xslot(k) : yslot(k);
         if (slot >= 0) {
             Real eq, src;
             f_eq_src(k, ph, s, eq, src);
-            out[slot * stride] = ph.ff_a * fb[k] + ph.ff_b * eq + ph.ff_c * src;
+            out[slot] = ph.ff_a * fb[k] + ph.ff_b * eq + ph.ff_c * src;
         }
     }
     if (COUPLED) {
-        const Real inv = Real(1) / (Real(2) * s.taug + ph.h);
+        const Real inv = rcp_r(Real(2) * s.taug + ph.h);
         const Real a = Real(2) * s.taug * inv, bb = ph.h * inv, c = s.taug * ph.h * inv;
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
+        for (int k = 1; k < 9; k++) {
             const int slot = XFACE ? xslot(k) : yslot(k);
             if (slot >= 0) {
                 Real eq, src;
                 g_eq_src(k, s, eq, src);
-                out[(6 + slot) * stride] = a * gb[k] + bb * eq + c * src;
+                out[6 + slot] = a * gb[k] + bb * eq + c * src;
             }
         }
+    }
+}
+
+template <typename Real, bool COUPLED, int FS>
+__device__ __forceinline__ void store_flux(Real *p, const Real v[12]) {
+    if (COUPLED) {
+        st4(p, v[0], v[1], v[2], v[3]);
+        st4(p + 4, v[4], v[5], v[6], v[7]);
+        st4(p + 8, v[8], v[9], v[10], v[11]);
+    } else {
+        st2(p, v[0], v[1]);
+        st2(p + 2, v[2], v[3]);
+        st2(p + 4, v[4], v[5]);
+    }
+}
+template <typename Real, bool COUPLED, int FS>
+__device__ __forceinline__ void load_flux(const Real *p, Real v[12]) {
+    if (COUPLED) {
+        ld4(p, v);
+        ld4(p + 4, v + 4);
+        ld4(p + 8, v + 8);
+    } else {
+        ld2(p, v);
+        ld2(p + 2, v + 2);
+        ld2(p + 4, v + 4);
     }
 }
 
@@ -313,148 +553,215 @@ __device__ __forceinline__ void phi_stencils(const Real *__restrict__ p, int c, 
     lp = (Real(4) * ((E + Wv) + (N + S)) + ((NE + NW) + (SE + SW)) - Real(20) * C) * Real(1.0 / 6.0);
 }
 
+// Macros, equilibria, sources and psi-bar-plus (Eq. 29) of one cell of the
+// halo-1 region (record index c1, box index e), from the staged box.  For a
+// tile cell (TILE) also psi~+ partials tp = 4/3 psi-bar-plus - 1/3 psi~
+// (Eq. 30) and the new (phi u) history.
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool TILE>
+__device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Real> &ph, const Real *__restrict__ box,
+                                          const Real *__restrict__ sphi, Real *__restrict__ rec, Real *__restrict__ aux,
+                                          Real *__restrict__ sdy, int hx, int hy, int x0, int y0, Real tp[18]) {
+    using S = TileShape<Real, TX, TY, COUPLED>;
+    using R = Rec<COUPLED>;
+    constexpr int RS = S::RS, AS = S::AS, BXY = S::BXY;
+    const int c1 = hy * S::HX1 + hx;
+    const int yraw = y0 + hy - 1;
+    if (WALLY && (yraw < 0 || yraw >= a.ny)) {
+        // outside the walls: never read by a face; keep the smem defined
+#pragma unroll
+        for (int G = 0; G < R::NG; G++) st4(rec + c1 * RS + 4 * G, Real(0), Real(0), Real(0), Real(0));
+        st4(aux + c1 * AS, Real(0), Real(0), Real(0), Real(0));
+        if (S::F64) aux[c1 * AS + 4] = Real(0); else sdy[c1] = Real(0);
+        return;
+    }
+    const int e = (hy + 1) * S::BX + hx + 3;
+    Pt<Real> s;
+    const int c2 = (hy + 1) * S::HX2 + (hx + 1);
+    phi_stencils(sphi, c2, S::HX2, s.dpx, s.dpy, s.lap);
+    s.phi = ph.phi_ref + sphi[c2];
+    closures<Real, COUPLED>(ph, s);
+    Real dg[9];
+    if (COUPLED) {
+#pragma unroll
+        for (int k = 0; k < 9; k++) dg[k] = box[(9 + k) * BXY + e];
+        Real mx, my, sn;
+        moments9(dg, mx, my, sn);
+        velocity_pressure(mx, my, sn, ph.half_dt, s);
+    } else {
+        s.ux = ph.u0x;
+        s.uy = ph.u0y;
+    }
+    const Real phux = s.phi * s.ux, phuy = s.phi * s.uy;
+    if (a.first_step) {
+        s.Dx = Real(0);
+        s.Dy = Real(0);
+    } else {
+        s.Dx = (phux - box[S::NQ * BXY + e]) * ph.inv_dt;
+        s.Dy = (phuy - box[(S::NQ + 1) * BXY + e]) * ph.inv_dt;
+    }
+    st4(aux + c1 * AS, s.dpx, s.dpy, s.lap, s.Dx);
+    if (S::F64) aux[c1 * AS + 4] = s.Dy; else sdy[c1] = s.Dy;
+
+    Real r[4 * R::NG];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        Real eq, src;
+        f_eq_src(k, ph, s, eq, src);
+        const Real d = box[k * BXY + e];
+        const Real bp = ph.pf_a * d + ph.pf_b * eq + ph.pf_c * src;
+        r[R::slot(0, k)] = bp;
+        if (TILE) tp[k] = Real(4.0 / 3.0) * bp - Real(1.0 / 3.0) * d;
+    }
+    if (COUPLED) {
+        const Real inv = rcp_r(Real(2) * s.taug + ph.dt);
+        const Real ca = (Real(2) * s.taug - ph.h) * inv, cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            Real eq, src;
+            g_eq_src(k, s, eq, src);
+            const Real bp = ca * dg[k] + cb * eq + cc * src;
+            r[R::slot(1, k)] = bp;
+            if (TILE) tp[9 + k] = Real(4.0 / 3.0) * bp - Real(1.0 / 3.0) * dg[k];
+        }
+    }
+#pragma unroll
+    for (int j = 4 * R::NG - 3; j < 4 * R::NG; j++)
+        if (!R::used(j)) r[j] = Real(0);
+#pragma unroll
+    for (int G = 0; G < R::NG; G++) st4(rec + c1 * RS + 4 * G, r[4 * G], r[4 * G + 1], r[4 * G + 2], r[4 * G + 3]);
+
+    if (TILE && x0 + hx - 1 < a.nx && yraw < a.ny) {
+        const long long g = (long long)yraw * a.pitch + (x0 + hx - 1);
+        a.hdst[g] = phux;
+        a.hdst[a.plane + g] = phuy;
+        const bool bad = !finite_r(s.phi) || !finite_r(s.ux) || !finite_r(s.uy);
+        const bool nonphys = COUPLED && !(s.rho > Real(0) && s.taug > Real(0));
+        if (bad || nonphys) atomicOr(a.status, (bad ? STATUS_NONFINITE : 0u) | (nonphys ? STATUS_NONPHYSICAL : 0u));
+    }
+}
+
+// Bound on mbarrier polls before a TMA wait gives up (well under a second).
+// After one CTA has timed out the status word carries STATUS_TIMEOUT and
+// later CTAs stage their box with plain loads instead.
+constexpr long kPollLimit = 1l << 16;
+
 // ---------------------------------------------------------------------------
 // The fused step: one CTA per TX x TY tile, one thread per tile cell.
-//   1. phi' = sum_i d^f_i on the tile + 2-cell halo (global -> smem)
+//   0. stage the input box (distributions and history, tile + halo) in smem:
+//      one TMA load per array for interior tiles, plain loads with periodic
+//      wrap / wall mirror for tiles touching the domain edge
+//   1. phi' = sum_i d^f_i on the tile + 2-cell halo
 //   2. cell macros, equilibria, sources and psi-bar-plus (Eq. 29) on the tile
-//      + 1-cell halo (smem); (phi u)^n of the tile to global
+//      + 1-cell halo (smem records); psi~+ partials of the tile cells stay in
+//      registers; (phi u)^n of the tile to global
 //   3. every face of the tile: reconstruction (Eq. 27), face macros, Eq. 28
-//   4. psi~+ (Eq. 30) and the flux update (Eq. 24) of the tile to global
+//      (face records reuse the box)
+//   4. the flux update (Eq. 24) of the tile to global
 // ---------------------------------------------------------------------------
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
 __global__ void __launch_bounds__(TX * TY)
-step_kernel(StepArgs<Real> a, Phys<Real> ph) {
+step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_constant__ CUtensorMap tm_hist,
+            StepArgs<Real> a, Phys<Real> ph) {
     using S = TileShape<Real, TX, TY, COUPLED>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real *sm = reinterpret_cast<Real *>(smem_raw);
+    constexpr int RS = S::RS, AS = S::AS, FS = S::FS, BX = S::BX, BXY = S::BXY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned base for the TMA destinations, whatever the runtime gives
+    Real *sm = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    Real *box = sm + S::off_box;
     Real *sphi = sm + S::off_phi;
-    Real *sbp = sm + S::off_bp;
-    Real *saux = sm + S::off_aux;
+    Real *rec = sm + S::off_rec;
+    Real *aux = sm + S::off_aux;
+    Real *sdy = sm + S::off_dy;
     Real *sfx = sm + S::off_fx;
     Real *sfy = sm + S::off_fy;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S::off_bar);
+    int *staged_ok = reinterpret_cast<int *>(bar + 1);
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
 
+    // 0. stage the input box [NQ + 2][BY][BX]
+    const bool interior = a.use_tma && x0 >= 4 && x0 + TX + 4 <= nx && y0 >= 2 && y0 + TY + 2 <= ny;
+    if (tid == 0) {
+        int mode = 0;  // 0: plain loads, 1: staged by TMA, 2: TMA timed out
+        if (interior && !(*((volatile unsigned *)a.status) & STATUS_TIMEOUT)) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, (uint32_t)((S::NQ + 2) * BXY * sizeof(Real)));
+            tma_load_3d(box, &tm_state, x0 - 4, y0 - 2, 0, bar);
+            tma_load_3d(box + S::NQ * BXY, &tm_hist, x0 - 4, y0 - 2, 0, bar);
+            mode = 1;
+            if (!mbar_wait(bar, 0, kPollLimit)) {
+                atomicOr(a.status, STATUS_TIMEOUT);
+                mbar_wait(bar, 0, kPollLimit);  // let copies in flight land before the CTA exits
+                mode = 2;
+            }
+        }
+        *staged_ok = mode;
+    }
+    __syncthreads();
+    const int mode = *staged_ok;
+    if (mode == 2) return;
+    if (mode == 1) {
+        mbar_wait(bar, 0, 1);  // completed phase: makes the TMA writes visible to this thread
+    } else {
+        for (int e = tid; e < (S::NQ + 2) * BXY; e += S::NT) {
+            const int z = e / BXY, r = e - z * BXY, by = r / BX, bx = r - by * BX;
+            const int gx = wrap(x0 - 4 + bx, nx);
+            const int gy = map_row<WALLY>(y0 - 2 + by, ny, true);
+            const long long g = (long long)gy * pitch + gx;
+            box[e] = z < S::NQ ? a.src[z * plane + g] : a.hsrc[(z - S::NQ) * plane + g];
+        }
+        __syncthreads();
+    }
+
     // 1. phi' on the halo-2 region
     for (int t = tid; t < S::N2; t += S::NT) {
         const int lx = t % S::HX2, ly = t / S::HX2;
-        const int gx = wrap(x0 + lx - 2, nx);
-        const int gy = map_row<WALLY>(y0 + ly - 2, ny);
-        const Real *p = a.src + (long long)gy * pitch + gx;
-        Real s = Real(0);
+        const Real *p = box + ly * BX + lx + 2;
+        Real s = p[0];
 #pragma unroll
-        for (int k = 0; k < 9; k++) s += p[k * plane];
+        for (int k = 1; k < 9; k++) s += p[k * BXY];
         sphi[t] = s;
     }
     __syncthreads();
 
-    // 2. cell macros and psi-bar-plus on the halo-1 region; item t < NT is tile cell t
-    for (int t = tid; t < S::N1; t += S::NT) {
+    // 2. the tile cell of this thread, then at most one halo-ring cell
+    Real tp[18];
+    cell_item<Real, TX, TY, COUPLED, WALLY, true>(a, ph, box, sphi, rec, aux, sdy, tid % TX + 1, tid / TX + 1, x0,
+                                                  y0, tp);
+    for (int t = tid + S::NT; t < S::N1; t += S::NT) {
+        const int r = t - S::NT;
         int hx, hy;
-        if (t < S::NT) {
-            hx = t % TX + 1;
-            hy = t / TX + 1;
-        } else {
-            const int r = t - S::NT;
-            if (r < S::HX1) { hx = r; hy = 0; }
-            else if (r < 2 * S::HX1) { hx = r - S::HX1; hy = S::HY1 - 1; }
-            else if (r < 2 * S::HX1 + TY) { hx = 0; hy = r - 2 * S::HX1 + 1; }
-            else { hx = S::HX1 - 1; hy = r - 2 * S::HX1 - TY + 1; }
-        }
-        const int c1 = hy * S::HX1 + hx;
-        const int yraw = y0 + hy - 1;
-        if (WALLY && (yraw < 0 || yraw >= ny)) {
-#pragma unroll
-            for (int k = 0; k < S::NQ; k++) sbp[k * S::N1 + c1] = Real(0);
-#pragma unroll
-            for (int k = 0; k < 5; k++) saux[k * S::N1 + c1] = Real(0);
-            continue;
-        }
-        const int gx = wrap(x0 + hx - 1, nx);
-        const int gy = WALLY ? yraw : wrap(yraw, ny);
-        const long long g = (long long)gy * pitch + gx;
-
-        Pt<Real> s;
-        const int c2 = (hy + 1) * S::HX2 + (hx + 1);
-        phi_stencils(sphi, c2, S::HX2, s.dpx, s.dpy, s.lap);
-        s.phi = ph.phi_ref + sphi[c2];
-        closures<Real, COUPLED>(ph, s);
-        Real dg[9];
-        if (COUPLED) {
-            Real mx = Real(0), my = Real(0), sn = Real(0);
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                dg[k] = a.src[(9 + k) * plane + g];
-                mx += Real(cx(k)) * dg[k];
-                my += Real(cy(k)) * dg[k];
-                if (k) sn += dg[k];
-            }
-            velocity_pressure(mx, my, sn, ph.half_dt, s);
-        } else {
-            s.ux = ph.u0x;
-            s.uy = ph.u0y;
-        }
-        const Real phux = s.phi * s.ux, phuy = s.phi * s.uy;
-        if (a.first_step) {
-            s.Dx = Real(0);
-            s.Dy = Real(0);
-        } else {
-            const Real idt = Real(1) / ph.dt;
-            s.Dx = (phux - a.hsrc[g]) * idt;
-            s.Dy = (phuy - a.hsrc[plane + g]) * idt;
-        }
-        saux[0 * S::N1 + c1] = s.dpx;
-        saux[1 * S::N1 + c1] = s.dpy;
-        saux[2 * S::N1 + c1] = s.lap;
-        saux[3 * S::N1 + c1] = s.Dx;
-        saux[4 * S::N1 + c1] = s.Dy;
-#pragma unroll
-        for (int k = 0; k < 9; k++) {
-            Real eq, src;
-            f_eq_src(k, ph, s, eq, src);
-            const Real d = a.src[k * plane + g];
-            sbp[k * S::N1 + c1] = ph.pf_a * d + ph.pf_b * eq + ph.pf_c * src;
-        }
-        if (COUPLED) {
-            const Real inv = Real(1) / (Real(2) * s.taug + ph.dt);
-            const Real ca = (Real(2) * s.taug - ph.h) * inv, cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                Real eq, src;
-                g_eq_src(k, s, eq, src);
-                sbp[(9 + k) * S::N1 + c1] = ca * dg[k] + cb * eq + cc * src;
-            }
-        }
-        if (t < S::NT && x0 + hx - 1 < nx && yraw < ny) {
-            a.hdst[g] = phux;
-            a.hdst[plane + g] = phuy;
-            bool bad = !finite_r(s.phi) || !finite_r(s.ux) || !finite_r(s.uy);
-            bool nonphys = COUPLED && !(s.rho > Real(0) && s.taug > Real(0));
-            if (bad || nonphys) atomicOr(a.status, (bad ? STATUS_NONFINITE : 0u) | (nonphys ? STATUS_NONPHYSICAL : 0u));
-        }
+        if (r < S::HX1) { hx = r; hy = 0; }
+        else if (r < 2 * S::HX1) { hx = r - S::HX1; hy = S::HY1 - 1; }
+        else if (r < 2 * S::HX1 + TY) { hx = 0; hy = r - 2 * S::HX1 + 1; }
+        else { hx = S::HX1 - 1; hy = r - 2 * S::HX1 - TY + 1; }
+        cell_item<Real, TX, TY, COUPLED, WALLY, false>(a, ph, box, sphi, rec, aux, sdy, hx, hy, x0, y0, nullptr);
     }
     __syncthreads();
 
     // 3. faces: x-faces (west face of local cell (fx, fy)), then y-faces (south face)
     for (int t = tid; t < S::NFX + S::NFY; t += S::NT) {
-        Real fb[9], gb[9];
+        Real fb[9], gb[9], out[12];
+        Real au[4], bu[4], ady, bdy;
         if (t < S::NFX) {
             const int fx = t % (TX + 1), fy = t / (TX + 1);
             const int gyr = y0 + fy;
             if (gyr >= ny || x0 + fx - 1 >= nx) continue;
-            const int L = (fy + 1) * S::HX1 + fx, R = L + 1;
+            const int L = (fy + 1) * S::HX1 + fx, Rr = L + 1;
             int tmode = 0;
             if (WALLY) tmode = (gyr == 0) ? 1 : ((gyr == ny - 1) ? -1 : 0);
-            recon9<Real, true>(sbp, S::N1, L, R, S::HX1, tmode, ph.h, fb);
-            if (COUPLED) recon9<Real, true>(sbp + 9 * S::N1, S::N1, L, R, S::HX1, tmode, ph.h, gb);
+            recon_face<Real, COUPLED, true, RS>(rec, L, Rr, S::HX1, tmode, ph.h, fb, gb);
+            ld4(aux + L * AS, au);
+            ld4(aux + Rr * AS, bu);
+            ady = S::F64 ? aux[L * AS + 4] : sdy[L];
+            bdy = S::F64 ? aux[Rr * AS + 4] : sdy[Rr];
             const Real hf = Real(0.5);
-            face_flux<Real, COUPLED, true>(
-                ph, fb, gb, hf * (saux[L] + saux[R]), hf * (saux[S::N1 + L] + saux[S::N1 + R]),
-                hf * (saux[2 * S::N1 + L] + saux[2 * S::N1 + R]), hf * (saux[3 * S::N1 + L] + saux[3 * S::N1 + R]),
-                hf * (saux[4 * S::N1 + L] + saux[4 * S::N1 + R]), false, sfx + t, S::NFX);
+            face_flux<Real, COUPLED, true>(ph, fb, gb, hf * (au[0] + bu[0]), hf * (au[1] + bu[1]), hf * (au[2] + bu[2]),
+                                           hf * (au[3] + bu[3]), hf * (ady + bdy), false, out);
+            store_flux<Real, COUPLED, FS>(sfx + t * FS, out);
         } else {
             const int u = t - S::NFX;
             const int fx = u % TX, fy = u / TX;
@@ -464,53 +771,63 @@ step_kernel(StepArgs<Real> a, Phys<Real> ph) {
             if (WALLY && (gyf == 0 || gyf == ny)) {
                 const bool top = (gyf == ny);
                 const int c0 = top ? D : U;
-                if (top) {
-                    recon_wall9<Real, true>(sbp, S::N1, c0, -S::HX1, ph.h, fb);
-                    if (COUPLED) recon_wall9<Real, true>(sbp + 9 * S::N1, S::N1, c0, -S::HX1, ph.h, gb);
-                } else {
-                    recon_wall9<Real, false>(sbp, S::N1, c0, S::HX1, ph.h, fb);
-                    if (COUPLED) recon_wall9<Real, false>(sbp + 9 * S::N1, S::N1, c0, S::HX1, ph.h, gb);
-                }
-                face_flux<Real, COUPLED, false>(ph, fb, gb, saux[c0], Real(0), saux[2 * S::N1 + c0],
-                                                saux[3 * S::N1 + c0], Real(0), true, sfy + u, S::NFY);
+                if (top)
+                    recon_wall<Real, COUPLED, true, RS>(rec, c0, -S::HX1, ph.h, fb, gb);
+                else
+                    recon_wall<Real, COUPLED, false, RS>(rec, c0, S::HX1, ph.h, fb, gb);
+                ld4(aux + c0 * AS, au);
+                face_flux<Real, COUPLED, false>(ph, fb, gb, au[0], Real(0), au[2], au[3], Real(0), true, out);
             } else {
-                recon9<Real, false>(sbp, S::N1, D, U, 1, 0, ph.h, fb);
-                if (COUPLED) recon9<Real, false>(sbp + 9 * S::N1, S::N1, D, U, 1, 0, ph.h, gb);
+                recon_face<Real, COUPLED, false, RS>(rec, D, U, 1, 0, ph.h, fb, gb);
+                ld4(aux + D * AS, au);
+                ld4(aux + U * AS, bu);
+                ady = S::F64 ? aux[D * AS + 4] : sdy[D];
+                bdy = S::F64 ? aux[U * AS + 4] : sdy[U];
                 const Real hf = Real(0.5);
-                face_flux<Real, COUPLED, false>(
-                    ph, fb, gb, hf * (saux[D] + saux[U]), hf * (saux[S::N1 + D] + saux[S::N1 + U]),
-                    hf * (saux[2 * S::N1 + D] + saux[2 * S::N1 + U]), hf * (saux[3 * S::N1 + D] + saux[3 * S::N1 + U]),
-                    hf * (saux[4 * S::N1 + D] + saux[4 * S::N1 + U]), false, sfy + u, S::NFY);
+                face_flux<Real, COUPLED, false>(ph, fb, gb, hf * (au[0] + bu[0]), hf * (au[1] + bu[1]),
+                                                hf * (au[2] + bu[2]), hf * (au[3] + bu[3]), hf * (ady + bdy), false, out);
             }
+            store_flux<Real, COUPLED, FS>(sfy + u * FS, out);
         }
     }
     __syncthreads();
 
-    // 4. psi~+ = 4/3 psi-bar-plus - 1/3 psi~ and the flux update of the tile
+    // 4. the flux update of the tile
     {
         const int lx = tid % TX, ly = tid / TX;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx < nx && gy < ny) {
             const long long g = (long long)gy * pitch + gx;
-            const int c1 = (ly + 1) * S::HX1 + lx + 1;
-            const int fw = ly * (TX + 1) + lx, fe = fw + 1;  // x-faces
-            const int fs = ly * TX + lx, fn = fs + TX;       // y-faces
+            const Real dt = ph.dt;
+            Real v[12];
+            // west (+) and east (-) x-faces
+            load_flux<Real, COUPLED, FS>(sfx + (ly * (TX + 1) + lx) * FS, v);
 #pragma unroll
-            for (int k = 0; k < S::NQ; k++) {
-                const int kk = k % 9, base = (k < 9) ? 0 : 6;
-                const Real d = a.src[k * plane + g];
-                const Real tp = Real(4.0 / 3.0) * sbp[k * S::N1 + c1] - Real(1.0 / 3.0) * d;
-                Real flux = Real(0);
-                if (cx(kk) != 0) {
-                    const Real *q = sfx + (base + xslot(kk)) * S::NFX;
-                    flux += Real(cx(kk)) * (q[fe] - q[fw]);
-                }
-                if (cy(kk) != 0) {
-                    const Real *q = sfy + (base + yslot(kk)) * S::NFY;
-                    flux += Real(cy(kk)) * (q[fn] - q[fs]);
-                }
-                a.dst[k * plane + g] = tp - ph.dt * flux;
+            for (int q = 0; q < S::NQ; q++) {
+                const int m = q / 9, k = q % 9;
+                if (cx(k) != 0) tp[q] += dt * sgnmul(cx(k), v[6 * m + xslot(k)]);
             }
+            load_flux<Real, COUPLED, FS>(sfx + (ly * (TX + 1) + lx + 1) * FS, v);
+#pragma unroll
+            for (int q = 0; q < S::NQ; q++) {
+                const int m = q / 9, k = q % 9;
+                if (cx(k) != 0) tp[q] -= dt * sgnmul(cx(k), v[6 * m + xslot(k)]);
+            }
+            // south (+) and north (-) y-faces
+            load_flux<Real, COUPLED, FS>(sfy + (ly * TX + lx) * FS, v);
+#pragma unroll
+            for (int q = 0; q < S::NQ; q++) {
+                const int m = q / 9, k = q % 9;
+                if (cy(k) != 0) tp[q] += dt * sgnmul(cy(k), v[6 * m + yslot(k)]);
+            }
+            load_flux<Real, COUPLED, FS>(sfy + ((ly + 1) * TX + lx) * FS, v);
+#pragma unroll
+            for (int q = 0; q < S::NQ; q++) {
+                const int m = q / 9, k = q % 9;
+                if (cy(k) != 0) tp[q] -= dt * sgnmul(cy(k), v[6 * m + yslot(k)]);
+            }
+#pragma unroll
+            for (int q = 0; q < S::NQ; q++) a.dst[q * plane + g] = tp[q];
         }
     }
 }

@@ -12,7 +12,8 @@ namespace dugks {
 template <typename Real> struct FieldArgs;
 
 template <typename Real>
-cudaError_t launch_step(const StepArgs<Real> &a, const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st);
+cudaError_t launch_step(const StepArgs<Real> &a, const Phys<Real> &ph, bool coupled, bool wally,
+                        const CUtensorMap *tm_state, const CUtensorMap *tm_hist, cudaStream_t st);
 template <typename Real>
 size_t step_smem_bytes(bool coupled);
 template <typename Real>

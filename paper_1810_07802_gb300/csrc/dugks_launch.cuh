@@ -9,14 +9,28 @@
 
 namespace dugks {
 
-// Tile shapes: FP64 favours square tiles (least halo recompute for an
-// ALU-bound step), FP32 wide tiles (full 128-byte rows per warp).
+// Tile shapes (build-time; measured on GB300, see profiles/): FP64 favours
+// square tiles (least halo recompute for an ALU-bound step), FP32 wide tiles
+// (full 128-byte rows per warp).
+#ifndef DUGKS_TILE_F64_X
+#define DUGKS_TILE_F64_X 16
+#endif
+#ifndef DUGKS_TILE_F64_Y
+#define DUGKS_TILE_F64_Y 8
+#endif
+#ifndef DUGKS_TILE_F32_X
+#define DUGKS_TILE_F32_X 32
+#endif
+#ifndef DUGKS_TILE_F32_Y
+#define DUGKS_TILE_F32_Y 8
+#endif
 template <typename Real> struct Tile;
-template <> struct Tile<double> { static constexpr int TX = 16, TY = 16; };
-template <> struct Tile<float> { static constexpr int TX = 32, TY = 8; };
+template <> struct Tile<double> { static constexpr int TX = DUGKS_TILE_F64_X, TY = DUGKS_TILE_F64_Y; };
+template <> struct Tile<float> { static constexpr int TX = DUGKS_TILE_F32_X, TY = DUGKS_TILE_F32_Y; };
 
 template <typename Real, bool COUPLED, bool WALLY>
-static cudaError_t launch_step_t(const StepArgs<Real> &a, const Phys<Real> &ph, cudaStream_t st) {
+static cudaError_t launch_step_t(const StepArgs<Real> &a, const Phys<Real> &ph, const CUtensorMap *tm_state,
+                                 const CUtensorMap *tm_hist, cudaStream_t st) {
     constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
     using S = TileShape<Real, TX, TY, COUPLED>;
     auto kern = step_kernel<Real, TX, TY, COUPLED, WALLY>;
@@ -24,14 +38,20 @@ static cudaError_t launch_step_t(const StepArgs<Real> &a, const Phys<Real> &ph, 
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
     if (attr != cudaSuccess) return attr;
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-    kern<<<grid, S::NT, S::smem_bytes, st>>>(a, ph);
+    StepArgs<Real> b = a;
+    b.small = (a.nx < TX + 4 || a.ny < TY + 4) ? 1 : 0;   // halo indices may wrap more than once
+    kern<<<grid, S::NT, S::smem_bytes, st>>>(*tm_state, *tm_hist, b, ph);
     return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_step(const StepArgs<Real> &a, const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st) {
-    if (coupled) return wally ? launch_step_t<Real, true, true>(a, ph, st) : launch_step_t<Real, true, false>(a, ph, st);
-    return wally ? launch_step_t<Real, false, true>(a, ph, st) : launch_step_t<Real, false, false>(a, ph, st);
+cudaError_t launch_step(const StepArgs<Real> &a, const Phys<Real> &ph, bool coupled, bool wally,
+                        const CUtensorMap *tm_state, const CUtensorMap *tm_hist, cudaStream_t st) {
+    if (coupled)
+        return wally ? launch_step_t<Real, true, true>(a, ph, tm_state, tm_hist, st)
+                     : launch_step_t<Real, true, false>(a, ph, tm_state, tm_hist, st);
+    return wally ? launch_step_t<Real, false, true>(a, ph, tm_state, tm_hist, st)
+                 : launch_step_t<Real, false, false>(a, ph, tm_state, tm_hist, st);
 }
 
 template <typename Real>
@@ -85,7 +105,8 @@ cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, doub
 }
 
 #define DUGKS_INSTANTIATE(Real)                                                                                     \
-    template cudaError_t launch_step<Real>(const StepArgs<Real> &, const Phys<Real> &, bool, bool, cudaStream_t);  \
+    template cudaError_t launch_step<Real>(const StepArgs<Real> &, const Phys<Real> &, bool, bool,                 \
+                                           const CUtensorMap *, const CUtensorMap *, cudaStream_t);                 \
     template size_t step_smem_bytes<Real>(bool);                                                                    \
     template int step_tile<Real>(int);                                                                              \
     template cudaError_t launch_init<Real>(const double *, Real *, Real *, int, int, int, long long,                \

@@ -53,6 +53,31 @@ def test_coupled_periodic_fp64(S, nx, ny, steps):
     assert_parity(got, ref, dist, st, what="%dx%d/%d" % (nx, ny, steps))
 
 
+@pytest.mark.parametrize("nx,ny,steps,bc_y", [(150, 70, 6, "periodic"), (131, 53, 9, "wall"), (96, 40, 4, "periodic")])
+def test_interior_tiles_fp64(S, nx, ny, steps, bc_y):
+    """Grids large enough for interior tiles, whose input box is staged by TMA
+    (edge tiles use plain loads): both paths in one run against the oracle."""
+    cfg, f = W.random_state(nx, ny, seed=nx + 3 * ny, bc_y=bc_y)
+    got, ref, dist, st = run_both(S, cfg, f, steps)
+    assert_parity(got, ref, dist, st, what="interior %dx%d %s" % (nx, ny, bc_y))
+
+
+@pytest.mark.parametrize("bc_y", ["periodic", "wall"])
+def test_interior_tiles_fp32(S, bc_y):
+    """FP32-shifted on a grid with interior (TMA-staged) tiles: within FP32
+    round-off of the FP64 oracle after a few steps."""
+    cfg, f = W.random_state(150, 70, seed=17, bc_y=bc_y)
+    with S.Solver(dict(cfg, precision="fp32", phi_ref=0.5), **f) as s:
+        s.step(6)
+        got = s.macros()
+    o = Oracle(cfg, **f)
+    o.step(6)
+    ref = o.macros()
+    assert np.abs(got["phi"] - ref["phi"]).max() <= 2e-5
+    assert np.abs(got["ux"] - ref["ux"]).max() <= 1e-7
+    assert np.abs(got["p"] - ref["p"]).max() <= 1e-5
+
+
 @pytest.mark.parametrize("nx,ny,steps", [(37, 29, 8), (20, 3, 5), (17, 33, 10), (40, 4, 3)])
 def test_coupled_walls_fp64(S, nx, ny, steps):
     cfg, f = W.random_state(nx, ny, seed=7 + nx, bc_y="wall")
