@@ -59,17 +59,15 @@ __global__ void init_kernel(const double *__restrict__ in, Real *__restrict__ st
     }
     s.Dx = 0.0;
     s.Dy = 0.0;
+    const FLin<double> lf = f_lin(ph, s, 1.0, -0.5 * ph.dt);   // f_eq - dt/2 S^f
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
-        double eq, src;
-        f_eq_src(k, ph, s, eq, src);
-        state[k * plane + g] = Real(eq - 0.5 * ph.dt * src);
-    }
+    for (int k = 0; k < 9; k++) state[k * plane + g] = Real(f_lin_k(k, lf));
     if (COUPLED) {
+        const GCoef<double> gc = g_coef(s);
 #pragma unroll
         for (int k = 0; k < 9; k++) {
             double eq, src;
-            g_eq_src(k, s, eq, src);
+            g_eq_src(k, s, gc, eq, src);
             state[(9 + k) * plane + g] = Real(eq - 0.5 * ph.dt * src);
         }
     }

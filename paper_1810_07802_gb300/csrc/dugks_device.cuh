@@ -161,38 +161,63 @@ __device__ __forceinline__ void velocity_pressure(Real mx, Real my, Real sn, Rea
                         - Real(2) / Real(3) * s.rho * (s.ux * s.ux + s.uy * s.uy));
 }
 
-// Deviation of f_eq (Eq. 15) and S^f (Eq. 16) in direction k.
+// The f model's equilibrium (Eq. 15, as a deviation from w_k phi_ref) and
+// source (Eq. 16) are linear in xi_k, so any combination c1 f_eq + c2 S^f is
+//     w_k (P + xi_k . V),  P = c1 (phi - phi_ref),
+//     V = 3 c1 phi u + c2 theta n + 3 c2 d_t(phi u)      (1 / RT = 3).
 template <typename Real>
-__device__ __forceinline__ void f_eq_src(int k, const Phys<Real> &ph, const Pt<Real> &s, Real &eq, Real &src) {
+struct FLin {
+    Real P, Vx, Vy;
+};
+template <typename Real>
+__device__ __forceinline__ FLin<Real> f_lin(const Phys<Real> &ph, const Pt<Real> &s, Real c1, Real c2) {
+    FLin<Real> r;
+    r.P = c1 * (s.phi - ph.phi_ref);
+    const Real a = Real(3) * c1 * s.phi, b = c2 * s.theta, c = Real(3) * c2;
+    r.Vx = a * s.ux + b * s.nx + c * s.Dx;
+    r.Vy = a * s.uy + b * s.ny + c * s.Dy;
+    return r;
+}
+template <typename Real>
+__device__ __forceinline__ Real f_lin_k(int k, const FLin<Real> &L) {
+    const Real w = wq<Real>(k);
+    if (k == 0) return w * L.P;
+    return w * (L.P + edot(k, L.Vx, L.Vy));
+}
+
+// Per-point terms of the g equilibrium (Eqs. 17-18) and source (Eq. 19)
+// shared by all directions.
+template <typename Real>
+struct GCoef {
+    Real usq15, udr, udf3, pd3, f3x, f3y;
+};
+template <typename Real>
+__device__ __forceinline__ GCoef<Real> g_coef(const Pt<Real> &s) {
+    GCoef<Real> c;
+    c.usq15 = Real(1.5) * (s.ux * s.ux + s.uy * s.uy);
+    c.udr = s.ux * s.drx + s.uy * s.dry;
+    c.f3x = Real(3) * s.Fx;
+    c.f3y = Real(3) * s.Fy;
+    c.udf3 = s.ux * c.f3x + s.uy * c.f3y;
+    c.pd3 = Real(3) * s.pd;
+    return c;
+}
+// Deviation of g_eq from 3 p_ref (w_k - delta_k0), and S^g, in direction k:
+//   Gamma_k - w_k = w_k (3 e + 4.5 e^2 - 1.5 |u|^2),  e = xi_k . u
+//   S^g_k = (Gamma_k - w_k)(xi_k - u).grad rho + 3 Gamma_k (xi_k - u).F
+template <typename Real>
+__device__ __forceinline__ void g_eq_src(int k, const Pt<Real> &s, const GCoef<Real> &c, Real &eq, Real &src) {
     const Real w = wq<Real>(k);
     if (k == 0) {
-        eq = w * (s.phi - ph.phi_ref);
-        src = Real(0);
+        const Real gam = w * (-c.usq15);
+        eq = c.pd3 * (w - Real(1)) + s.rho * gam;
+        src = -(gam * c.udr + (w + gam) * c.udf3);
         return;
     }
     const Real eu = edot(k, s.ux, s.uy);
-    eq = w * ((s.phi - ph.phi_ref) + Real(3) * s.phi * eu);
-    src = w * (s.theta * edot(k, s.nx, s.ny) + Real(3) * edot(k, s.Dx, s.Dy));
-}
-
-// Deviation of g_eq (Eqs. 17-18) and S^g (Eq. 19) in direction k.
-template <typename Real>
-__device__ __forceinline__ void g_eq_src(int k, const Pt<Real> &s, Real &eq, Real &src) {
-    const Real w = wq<Real>(k);
-    const Real usq = s.ux * s.ux + s.uy * s.uy;
-    Real gam;  // Gamma_k(u) - w_k
-    if (k == 0) {
-        gam = w * (Real(-1.5) * usq);
-        eq = Real(3) * s.pd * (w - Real(1)) + s.rho * gam;
-    } else {
-        const Real eu = edot(k, s.ux, s.uy);
-        gam = w * (eu * (Real(3) + Real(4.5) * eu) - Real(1.5) * usq);
-        eq = Real(3) * s.pd * w + s.rho * gam;
-    }
-    const Real G = w + gam;
-    const Real A = gam * s.drx + Real(3) * s.Fx * G;
-    const Real B = gam * s.dry + Real(3) * s.Fy * G;
-    src = eminus(cx(k), s.ux) * A + eminus(cy(k), s.uy) * B;
+    const Real gam = w * (eu * (Real(3) + Real(4.5) * eu) - c.usq15);
+    eq = c.pd3 * w + s.rho * gam;
+    src = gam * (edot(k, s.drx, s.dry) - c.udr) + (w + gam) * (edot(k, c.f3x, c.f3y) - c.udf3);
 }
 
 __device__ __forceinline__ int wrap(int x, int n) {
@@ -384,6 +409,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long m
 template <typename Real, bool COUPLED, bool XFACE, int RS>
 __device__ __forceinline__ void recon_face(const Real *__restrict__ rec, int A, int B, int tstride, int tmode, Real h,
                                            Real fb[9], Real gb[9]) {
+    // value - h xi.slope = (1/2 + h c_n) a + (1/2 - h c_n) b - h c_t s_t
+    const Real cp = Real(0.5) + h, cm = Real(0.5) - h;
+    const Real ht = tmode == 0 ? Real(0.25) * h : Real(0.5) * h;
 #pragma unroll
     for (int G = 0; G < Rec<COUPLED>::NG; G++) {
         Real a[4], b[4], an[4], as[4], bn[4], bs[4];
@@ -407,17 +435,16 @@ __device__ __forceinline__ void recon_face(const Real *__restrict__ rec, int A, 
             const int k = Rec<COUPLED>::dir(s), m = Rec<COUPLED>::model(s);
             if (m == 1 && k == 0) continue;
             const int cn = XFACE ? cx(k) : cy(k), ct = XFACE ? cy(k) : cx(k);
-            Real v = Real(0.5) * (a[j] + b[j]);
-            if (cn != 0) v -= h * sgnmul(cn, b[j] - a[j]);
+            Real v;
+            if (cn == 0) v = Real(0.5) * (a[j] + b[j]);
+            else if (cn > 0) v = cp * a[j] + cm * b[j];
+            else v = cm * a[j] + cp * b[j];
             if (ct != 0) {
-                Real st;
-                if (tmode == 0)
-                    st = Real(0.25) * ((an[j] - as[j]) + (bn[j] - bs[j]));
-                else if (tmode > 0)
-                    st = Real(0.5) * ((an[j] - a[j]) + (bn[j] - b[j]));
-                else
-                    st = Real(0.5) * ((a[j] - as[j]) + (b[j] - bs[j]));
-                v -= h * sgnmul(ct, st);
+                Real T;  // 4 s_t (central) or 2 s_t (one-sided)
+                if (tmode == 0) T = (an[j] + bn[j]) - (as[j] + bs[j]);
+                else if (tmode > 0) T = (an[j] + bn[j]) - (a[j] + b[j]);
+                else T = (a[j] + b[j]) - (as[j] + bs[j]);
+                v = ct > 0 ? v - ht * T : v + ht * T;
             }
             if (m == 0) fb[k] = v; else gb[k] = v;
         }
@@ -493,24 +520,22 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
         s.ux = wall ? Real(0) : ph.u0x;
         s.uy = wall ? Real(0) : ph.u0y;
     }
+    const FLin<Real> lf = f_lin(ph, s, ph.ff_b, ph.ff_c);
 #pragma unroll
     for (int k = 1; k < 9; k++) {
         const int slot = XFACE ? xslot(k) : yslot(k);
-        if (slot >= 0) {
-            Real eq, src;
-            f_eq_src(k, ph, s, eq, src);
-            out[slot] = ph.ff_a * fb[k] + ph.ff_b * eq + ph.ff_c * src;
-        }
+        if (slot >= 0) out[slot] = ph.ff_a * fb[k] + f_lin_k(k, lf);
     }
     if (COUPLED) {
         const Real inv = rcp_r(Real(2) * s.taug + ph.h);
         const Real a = Real(2) * s.taug * inv, bb = ph.h * inv, c = s.taug * ph.h * inv;
+        const GCoef<Real> gc = g_coef(s);
 #pragma unroll
         for (int k = 1; k < 9; k++) {
             const int slot = XFACE ? xslot(k) : yslot(k);
             if (slot >= 0) {
                 Real eq, src;
-                g_eq_src(k, s, eq, src);
+                g_eq_src(k, s, gc, eq, src);
                 out[6 + slot] = a * gb[k] + bb * eq + c * src;
             }
         }
@@ -603,22 +628,22 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
     if (S::F64) aux[c1 * AS + 4] = s.Dy; else sdy[c1] = s.Dy;
 
     Real r[4 * R::NG];
+    const FLin<Real> lf = f_lin(ph, s, ph.pf_b, ph.pf_c);
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-        Real eq, src;
-        f_eq_src(k, ph, s, eq, src);
         const Real d = box[k * BXY + e];
-        const Real bp = ph.pf_a * d + ph.pf_b * eq + ph.pf_c * src;
+        const Real bp = ph.pf_a * d + f_lin_k(k, lf);
         r[R::slot(0, k)] = bp;
         if (TILE) tp[k] = Real(4.0 / 3.0) * bp - Real(1.0 / 3.0) * d;
     }
     if (COUPLED) {
         const Real inv = rcp_r(Real(2) * s.taug + ph.dt);
         const Real ca = (Real(2) * s.taug - ph.h) * inv, cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
+        const GCoef<Real> gc = g_coef(s);
 #pragma unroll
         for (int k = 0; k < 9; k++) {
             Real eq, src;
-            g_eq_src(k, s, eq, src);
+            g_eq_src(k, s, gc, eq, src);
             const Real bp = ca * dg[k] + cb * eq + cc * src;
             r[R::slot(1, k)] = bp;
             if (TILE) tp[9 + k] = Real(4.0 / 3.0) * bp - Real(1.0 / 3.0) * dg[k];
