@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -233,6 +234,36 @@ def run_e2e(steps, f_host=None):
             "steps": steps, "region": "dugks_create(host phi0) + dugks_step(K) + dugks_macros(host)"}
 
 
+def run_serving(n=100, rate=50.0):
+    """The serving mix (Poiseuille / bubble / spinodal requests, Poisson
+    arrivals): continuous batching (FP32-shifted) against one solve at a time
+    (FP32 and FP64), and the same requests as one burst."""
+    from paper_1810_07802_gb300 import workloads as W
+    from paper_1810_07802_gb300.serve import BatchingServer, Request, SequentialServer, summary
+
+    def requests(precision, burst):
+        tr = W.serving_trace(n=n, rate=rate, precision=precision, burst=burst)
+        return [Request(i, k, c, f, st, t) for i, (k, c, f, st, t) in enumerate(tr)]
+
+    def keep(d):
+        return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in d.items()}
+
+    budget = 64 << 30
+    warm = requests("fp32", True)[:6]
+    BatchingServer(budget, keep_results=False).run(warm)
+    SequentialServer(keep_results=False).run(warm)
+    out = {"workload": "%d requests: layered Poiseuille (Ny 64-512, Nx 4, 400 steps), stationary bubbles "
+                       "(N 64-512, ratio 10/100/1000, 100 steps), spinodal boxes (N 128-1024, 200 steps)" % n,
+           "hbm_budget_bytes": budget}
+    for label, burst in (("poisson_%g_per_s" % rate, False), ("burst", True)):
+        r32, r64 = requests("fp32", burst), requests("fp64", burst)
+        out[label] = {"batched_fp32": keep(summary(BatchingServer(budget, max_members=128, chunk=50,
+                                                                  keep_results=False).run(r32))),
+                      "sequential_fp32": keep(summary(SequentialServer(keep_results=False).run(r32))),
+                      "sequential_fp64": keep(summary(SequentialServer(keep_results=False).run(r64)))}
+    return out
+
+
 def cpu_baseline_sample(rows=REF_BAND_ROWS, steps=2):
     """The FP64 oracle, as it stands, on a 2048 x rows band of the workload."""
     from oracle.oracle import Oracle
@@ -299,6 +330,8 @@ def ours(args):
             "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps}
     if rank == 0:
         line["e2e"] = run_e2e(args.steps)
+        if not args.no_serving:
+            line["serving"] = run_serving()
         if not args.no_cpu_baseline:
             rows, nst = 1024, 5
             v, dt, _ = cpu_baseline_sample(rows=rows, steps=nst)

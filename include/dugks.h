@@ -146,6 +146,35 @@ dugks_status dugks_sync(dugks_handle h);
 /* Frees the handle and the memory the library allocated.  Synchronises. */
 dugks_status dugks_destroy(dugks_handle h);
 
+/* ---- Batches: several independent problems advanced together ----
+ * A batch advances every member by the same number of DUGKS steps with one
+ * launch per kernel variant (precision x model x y-boundary) per step, over a
+ * work list of (problem, tile) items, captured once into a CUDA graph and
+ * replayed until the membership changes.  Each CTA runs the same tile code as
+ * dugks_step, so a member's result is bit-identical to stepping it alone.
+ * Members may differ in size, physics and precision.  While a handle is in a
+ * batch, advance it only through the batch; its other calls (dugks_macros,
+ * dugks_reduce, ...) stay valid but run on the handle's own stream, so use
+ * the batch's stream for the handle or call dugks_batch_sync first.  The
+ * batch does not own its members: remove or keep them, then destroy them
+ * with dugks_destroy. */
+typedef struct dugks_batch_ctx *dugks_batch;
+
+/* New empty batch enqueuing on cuda_stream (cudaStream_t or NULL). */
+dugks_status dugks_batch_create(void *cuda_stream, dugks_batch *out);
+/* Adds / removes a member (DUGKS_ERR_ARG if already in / not in the batch). */
+dugks_status dugks_batch_add(dugks_batch b, dugks_handle h);
+dugks_status dugks_batch_remove(dugks_batch b, dugks_handle h);
+/* Number of members, or -1 for a NULL batch. */
+int32_t dugks_batch_size(dugks_batch b);
+/* Enqueues nsteps >= 0 steps of every member (asynchronous).  The first call
+ * after a membership change uploads the work lists and captures the graph. */
+dugks_status dugks_batch_step(dugks_batch b, int64_t nsteps);
+/* Waits for the batch's stream; returns the first member's error status. */
+dugks_status dugks_batch_sync(dugks_batch b);
+/* Frees the batch (not its members).  Synchronises. */
+dugks_status dugks_batch_destroy(dugks_batch b);
+
 /* Allocation-free FP64 reduction of macro fields (the paper has no
  * counterpart; this is a convenience for callers that cannot allocate).
  * Some callers cannot call cudaMalloc/cudaFree where they need a convergence

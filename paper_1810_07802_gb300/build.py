@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libdugks_gb300.so"
 LIB_PATH = os.path.join(BUILD_DIR, LIB_NAME)
-SOURCES = ["dugks_capi.cu", "dugks_fp64.cu", "dugks_fp32.cu", "dugks_static.cu"]
+SOURCES = ["dugks_capi.cu", "dugks_fp64.cu", "dugks_fp32.cu", "dugks_static.cu", "dugks_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

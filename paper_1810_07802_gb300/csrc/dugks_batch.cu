@@ -1,0 +1,217 @@
+// dugks_batch.cu -- batches of independent solvers advanced together.
+//
+// Members are grouped by kernel variant (precision x model x y-boundary).
+// Each group owns a device array of per-problem descriptors (buffers,
+// constants, tensor maps, step counter) and a work list of (problem, tile)
+// items; one batched step is one launch per non-empty group plus a tiny
+// launch that swaps every member's ping-pong buffers.  The launches of one
+// step are captured once into a CUDA graph and replayed until membership
+// changes.  The CTAs run exactly the single-problem tile code, so each
+// member's result is identical to stepping it alone.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dugks.h"
+#include "dugks_internal.h"
+
+using dugks::InstDesc;
+using dugks::fill_desc;
+
+namespace {
+
+struct Group {
+    bool fp32 = false, coupled = false, wally = false;
+    std::vector<dugks_ctx *> members;
+    std::vector<unsigned char> h_desc;   // host image of the descriptor array
+    std::vector<int2> h_work;
+    void *d_desc = nullptr;
+    int2 *d_work = nullptr;
+    size_t desc_cap = 0, work_cap = 0;   // bytes / items allocated
+    int nwork = 0;
+};
+
+size_t desc_size(bool fp32) { return fp32 ? sizeof(InstDesc<float>) : sizeof(InstDesc<double>); }
+
+dugks_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return DUGKS_OK;
+    return e == cudaErrorMemoryAllocation ? DUGKS_ERR_OOM : DUGKS_ERR_CUDA;
+}
+
+}  // namespace
+
+struct dugks_batch_ctx {
+    cudaStream_t st = nullptr;
+    std::vector<dugks_ctx *> members;
+    Group groups[8];   // index: fp32 * 4 + coupled * 2 + wally
+    bool dirty = true;
+    cudaGraphExec_t exec = nullptr;
+
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+
+    // Rebuilds the host images (descriptors always, work lists when dirty) and uploads them.
+    cudaError_t upload() {
+        for (int gi = 0; gi < 8; gi++) {
+            Group &g = groups[gi];
+            if (dirty) {
+                g.fp32 = gi & 4;
+                g.coupled = gi & 2;
+                g.wally = gi & 1;
+                g.members.clear();
+                for (dugks_ctx *c : members)
+                    if (c->fp32 == g.fp32 && c->coupled == g.coupled && c->wally == g.wally) g.members.push_back(c);
+                const int tx = g.fp32 ? dugks::step_tile<float>(0) : dugks::step_tile<double>(0);
+                const int ty = g.fp32 ? dugks::step_tile<float>(1) : dugks::step_tile<double>(1);
+                g.h_work.clear();
+                for (size_t i = 0; i < g.members.size(); i++) {
+                    const dugks_ctx *c = g.members[i];
+                    const int n = ((c->P.nx + tx - 1) / tx) * ((c->P.ny + ty - 1) / ty);
+                    for (int t = 0; t < n; t++) g.h_work.push_back(make_int2((int)i, t));
+                }
+                g.nwork = (int)g.h_work.size();
+            }
+            if (g.members.empty()) continue;
+            const size_t ds = desc_size(g.fp32);
+            g.h_desc.assign(ds * g.members.size(), 0);
+            const int tx = g.fp32 ? dugks::step_tile<float>(0) : dugks::step_tile<double>(0);
+            for (size_t i = 0; i < g.members.size(); i++) {
+                const dugks_ctx *c = g.members[i];
+                if (g.fp32)
+                    fill_desc(reinterpret_cast<InstDesc<float> *>(g.h_desc.data()) + i, c, c->phf, tx);
+                else
+                    fill_desc(reinterpret_cast<InstDesc<double> *>(g.h_desc.data()) + i, c, c->phd, tx);
+            }
+            // grow the device arrays (capacity doubling; the graph holds their addresses)
+            if (g.h_desc.size() > g.desc_cap) {
+                drop_graph();
+                if (g.d_desc) cudaFree(g.d_desc);
+                g.desc_cap = std::max(g.h_desc.size(), 2 * g.desc_cap);
+                cudaError_t e = cudaMalloc(&g.d_desc, g.desc_cap);
+                if (e != cudaSuccess) { g.d_desc = nullptr; g.desc_cap = 0; return e; }
+            }
+            if (g.h_work.size() > g.work_cap) {
+                drop_graph();
+                if (g.d_work) cudaFree(g.d_work);
+                g.work_cap = std::max(g.h_work.size(), 2 * g.work_cap);
+                cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g.d_work), g.work_cap * sizeof(int2));
+                if (e != cudaSuccess) { g.d_work = nullptr; g.work_cap = 0; return e; }
+            }
+            cudaError_t e = cudaMemcpyAsync(g.d_desc, g.h_desc.data(), g.h_desc.size(), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && dirty)
+                e = cudaMemcpyAsync(g.d_work, g.h_work.data(), g.h_work.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+        }
+        if (dirty) drop_graph();
+        dirty = false;
+        return cudaSuccess;
+    }
+
+    // One batched step: every non-empty group's launch and buffer swap.
+    cudaError_t enqueue_step() {
+        for (Group &g : groups) {
+            if (g.members.empty()) continue;
+            cudaError_t e = g.fp32 ? dugks::launch_batch_step<float>(static_cast<InstDesc<float> *>(g.d_desc), g.d_work,
+                                                                     g.nwork, (int)g.members.size(), g.coupled,
+                                                                     g.wally, st)
+                                   : dugks::launch_batch_step<double>(static_cast<InstDesc<double> *>(g.d_desc),
+                                                                      g.d_work, g.nwork, (int)g.members.size(),
+                                                                      g.coupled, g.wally, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+
+    cudaError_t capture() {
+        for (Group &g : groups) {
+            if (g.members.empty()) continue;
+            cudaError_t e = g.fp32 ? dugks::batch_prepare<float>(g.coupled, g.wally)
+                                   : dugks::batch_prepare<double>(g.coupled, g.wally);
+            if (e != cudaSuccess) return e;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t el = enqueue_step();
+        e = cudaStreamEndCapture(st, &graph);
+        if (el != cudaSuccess) e = el;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) exec = nullptr;
+        return e;
+    }
+};
+
+extern "C" {
+
+dugks_status dugks_batch_create(void *cuda_stream, dugks_batch *out) {
+    if (!out) return DUGKS_ERR_ARG;
+    *out = nullptr;
+    dugks_batch_ctx *b = new (std::nothrow) dugks_batch_ctx();
+    if (!b) return DUGKS_ERR_OOM;
+    b->st = static_cast<cudaStream_t>(cuda_stream);
+    *out = b;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_batch_add(dugks_batch b, dugks_handle h) {
+    if (!b || !h) return DUGKS_ERR_ARG;
+    if (std::find(b->members.begin(), b->members.end(), h) != b->members.end()) return DUGKS_ERR_ARG;
+    b->members.push_back(h);
+    b->dirty = true;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_batch_remove(dugks_batch b, dugks_handle h) {
+    if (!b || !h) return DUGKS_ERR_ARG;
+    auto it = std::find(b->members.begin(), b->members.end(), h);
+    if (it == b->members.end()) return DUGKS_ERR_ARG;
+    b->members.erase(it);
+    b->dirty = true;
+    return DUGKS_OK;
+}
+
+int32_t dugks_batch_size(dugks_batch b) { return b ? (int32_t)b->members.size() : -1; }
+
+dugks_status dugks_batch_step(dugks_batch b, int64_t nsteps) {
+    if (!b || nsteps < 0) return DUGKS_ERR_ARG;
+    if (nsteps == 0 || b->members.empty()) return DUGKS_OK;
+    cudaError_t e = b->upload();
+    if (e == cudaSuccess && !b->exec) e = b->capture();
+    for (int64_t n = 0; n < nsteps && e == cudaSuccess; n++) e = cudaGraphLaunch(b->exec, b->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (dugks_ctx *c : b->members) {
+        c->steps += nsteps;
+        c->cur ^= (int)(nsteps & 1);
+    }
+    return DUGKS_OK;
+}
+
+dugks_status dugks_batch_sync(dugks_batch b) {
+    if (!b) return DUGKS_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    dugks_status worst = DUGKS_OK;
+    for (dugks_ctx *c : b->members) {
+        dugks_status s = dugks_sync(c);
+        if (s != DUGKS_OK && worst == DUGKS_OK) worst = s;
+    }
+    return worst;
+}
+
+dugks_status dugks_batch_destroy(dugks_batch b) {
+    if (!b) return DUGKS_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->st);
+    b->drop_graph();
+    for (Group &g : b->groups) {
+        if (g.d_desc) cudaFree(g.d_desc);
+        if (g.d_work) cudaFree(g.d_work);
+    }
+    delete b;
+    return from_cuda(e);
+}
+
+}  // extern "C"

@@ -2,9 +2,11 @@
 // workspace layout, stream-ordered launches and host<->device transfers.
 // All arithmetic of the scheme runs in the kernels (dugks_device.cuh,
 // dugks_aux.cuh); this file only marshals.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -15,6 +17,7 @@
 #include "dugks_reduce.cuh"
 
 using dugks::FieldArgs;
+using dugks::Layout;
 using dugks::Phys;
 using dugks::StepArgs;
 
@@ -35,11 +38,7 @@ constexpr uint64_t kStateVersion = 1;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-struct Layout {
-    int nq, pitch;
-    size_t elt, plane, n;
-    size_t off_state[2], off_hist[2], off_stage, off_phid, off_snap, off_partial, off_redout, off_status, total;
-};
+
 
 bool valid(const dugks_params *p) {
     if (!p) return false;
@@ -85,6 +84,7 @@ Layout layout(const dugks_params *p) {
     L.off_partial = o; o = align_up(o + (size_t)dugks::RED_BLOCKS * dugks::RED_VALS * sizeof(double), kAlign);
     L.off_redout = o;  o = align_up(o + 8 * sizeof(double), kAlign);
     L.off_status = o;  o = align_up(o + sizeof(unsigned), kAlign);
+    L.off_desc = o;    o = align_up(o + std::max(sizeof(dugks::InstDesc<double>), sizeof(dugks::InstDesc<float>)), kAlign);
     L.total = o;
     return L;
 }
@@ -169,43 +169,7 @@ bool make_box_map(CUtensorMap *m, void *base, bool f64, int nx, int ny, int pitc
 
 }  // namespace
 
-struct dugks_ctx {
-    dugks_params P;
-    Layout L;
-    bool fp32, coupled, wally;
-    cudaStream_t st;
-    unsigned char *ws;
-    bool owns;
-    int cur;
-    int64_t steps;
-    int have_snap;
-    unsigned status_seen;
-    Phys<double> phd;
-    Phys<float> phf;
-    bool tma_ok;
-    CUtensorMap tm_state[2], tm_hist[2];
 
-    void *state(int b) const { return ws + L.off_state[b]; }
-    void *hist(int b) const { return ws + L.off_hist[b]; }
-    double *stage() const { return reinterpret_cast<double *>(ws + L.off_stage); }
-    double *phid() const { return reinterpret_cast<double *>(ws + L.off_phid); }
-    double *snap() const { return reinterpret_cast<double *>(ws + L.off_snap); }
-    double *partial() const { return reinterpret_cast<double *>(ws + L.off_partial); }
-    double *redout() const { return reinterpret_cast<double *>(ws + L.off_redout); }
-    unsigned *status() const { return reinterpret_cast<unsigned *>(ws + L.off_status); }
-
-    template <typename Real>
-    FieldArgs<Real> fields() const {
-        FieldArgs<Real> a;
-        a.state = static_cast<const Real *>(state(cur));
-        a.hist = static_cast<const Real *>(hist(cur));
-        a.nx = P.nx;
-        a.ny = P.ny;
-        a.pitch = L.pitch;
-        a.plane = (long long)L.plane;
-        return a;
-    }
-};
 
 namespace {
 
@@ -289,7 +253,16 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
                                                   L.pitch, 2, tx + 8, ty + 4);
         }
     }
-    cudaError_t e = cudaMemsetAsync(c->ws, 0, L.off_stage, c->st);  // state, history (incl. row padding)
+    // the step kernel's descriptor of this problem (buffers, constants, tensor maps)
+    std::vector<unsigned char> desc_img(std::max(sizeof(dugks::InstDesc<double>), sizeof(dugks::InstDesc<float>)));
+    if (c->fp32)
+        dugks::fill_desc(reinterpret_cast<dugks::InstDesc<float> *>(desc_img.data()), c, c->phf,
+                         dugks::step_tile<float>(0));
+    else
+        dugks::fill_desc(reinterpret_cast<dugks::InstDesc<double> *>(desc_img.data()), c, c->phd,
+                         dugks::step_tile<double>(0));
+    cudaError_t e = cudaMemcpyAsync(c->desc(), desc_img.data(), desc_img.size(), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws, 0, L.off_stage, c->st);  // state, history (incl. row padding)
     const size_t fb = L.n * sizeof(double);
     double *in = c->stage();
     const double *src[4] = {phi0, ux0, uy0, p0};
@@ -324,42 +297,14 @@ dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
     if (!c || nsteps < 0) return DUGKS_ERR_ARG;
     for (int64_t n = 0; n < nsteps; n++) {
         cudaError_t e;
-        const int nxt = c->cur ^ 1;
-        if (c->fp32) {
-            StepArgs<float> a;
-            a.src = static_cast<const float *>(c->state(c->cur));
-            a.dst = static_cast<float *>(c->state(nxt));
-            a.hsrc = static_cast<const float *>(c->hist(c->cur));
-            a.hdst = static_cast<float *>(c->hist(nxt));
-            a.nx = c->P.nx;
-            a.ny = c->P.ny;
-            a.pitch = c->L.pitch;
-            a.plane = (long long)c->L.plane;
-            a.first_step = c->steps == 0;
-            a.small = 1;
-            a.use_tma = c->tma_ok;
-            a.status = c->status();
-            e = dugks::launch_step<float>(a, c->phf, c->coupled, c->wally, &c->tm_state[c->cur], &c->tm_hist[c->cur],
-                                          c->st);
-        } else {
-            StepArgs<double> a;
-            a.src = static_cast<const double *>(c->state(c->cur));
-            a.dst = static_cast<double *>(c->state(nxt));
-            a.hsrc = static_cast<const double *>(c->hist(c->cur));
-            a.hdst = static_cast<double *>(c->hist(nxt));
-            a.nx = c->P.nx;
-            a.ny = c->P.ny;
-            a.pitch = c->L.pitch;
-            a.plane = (long long)c->L.plane;
-            a.first_step = c->steps == 0;
-            a.small = 1;
-            a.use_tma = c->tma_ok;
-            a.status = c->status();
-            e = dugks::launch_step<double>(a, c->phd, c->coupled, c->wally, &c->tm_state[c->cur],
-                                           &c->tm_hist[c->cur], c->st);
-        }
+        if (c->fp32)
+            e = dugks::launch_step<float>(static_cast<const dugks::InstDesc<float> *>(c->desc()), c->P.nx, c->P.ny,
+                                          c->cur, c->steps, c->coupled, c->wally, c->st);
+        else
+            e = dugks::launch_step<double>(static_cast<const dugks::InstDesc<double> *>(c->desc()), c->P.nx,
+                                           c->P.ny, c->cur, c->steps, c->coupled, c->wally, c->st);
         if (e != cudaSuccess) return from_cuda(e);
-        c->cur = nxt;
+        c->cur ^= 1;
         c->steps++;
     }
     return DUGKS_OK;

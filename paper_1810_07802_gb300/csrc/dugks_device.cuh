@@ -352,6 +352,9 @@ struct TileShape {
     static_assert(off_fy + size_t(FS) * NFY <= off_phi, "face fluxes must fit in the input box");
     static_assert((size_t(NQ) * BXY * sizeof(Real)) % 128 == 0, "TMA destinations must be 128-byte aligned");
     static_assert((BX * sizeof(Real)) % 16 == 0, "TMA box rows must be multiples of 16 bytes");
+    // CTAs per SM that the shared memory allows (228 KiB per SM, 1 KiB reserved per CTA);
+    // passed to __launch_bounds__ so registers do not lower the occupancy further
+    static constexpr int MINB = (smem_bytes + 1024) * 3 <= 233472 ? 3 : ((smem_bytes + 1024) * 2 <= 233472 ? 2 : 1);
 };
 
 // ---- TMA (cp.async.bulk.tensor) and mbarrier helpers ----
@@ -684,9 +687,8 @@ constexpr long kPollLimit = 1l << 16;
 //   4. the flux update (Eq. 24) of the tile to global
 // ---------------------------------------------------------------------------
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
-__global__ void __launch_bounds__(TX * TY)
-step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_constant__ CUtensorMap tm_hist,
-            StepArgs<Real> a, Phys<Real> ph) {
+__device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
+                                          const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0) {
     using S = TileShape<Real, TX, TY, COUPLED>;
     constexpr int RS = S::RS, AS = S::AS, FS = S::FS, BX = S::BX, BXY = S::BXY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -703,7 +705,6 @@ step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_constant_
     int *staged_ok = reinterpret_cast<int *>(bar + 1);
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
 
@@ -714,8 +715,8 @@ step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_constant_
         if (interior && !(*((volatile unsigned *)a.status) & STATUS_TIMEOUT)) {
             mbar_init(bar, 1);
             mbar_expect_tx(bar, (uint32_t)((S::NQ + 2) * BXY * sizeof(Real)));
-            tma_load_3d(box, &tm_state, x0 - 4, y0 - 2, 0, bar);
-            tma_load_3d(box + S::NQ * BXY, &tm_hist, x0 - 4, y0 - 2, 0, bar);
+            tma_load_3d(box, tm_state_p, x0 - 4, y0 - 2, 0, bar);
+            tma_load_3d(box + S::NQ * BXY, tm_hist_p, x0 - 4, y0 - 2, 0, bar);
             mode = 1;
             if (!mbar_wait(bar, 0, kPollLimit)) {
                 atomicOr(a.status, STATUS_TIMEOUT);
@@ -854,6 +855,68 @@ step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_constant_
 #pragma unroll
             for (int q = 0; q < S::NQ; q++) a.dst[q * plane + g] = tp[q];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The step kernel, for one problem or a batch of independent problems of the
+// same precision, model and y-boundary.  Each CTA runs one tile:
+//   * work == nullptr: one problem (descs[0]), CTA b takes tile b (x-major);
+//     its buffer parity and step count come from the launch (cur_override,
+//     steps_override), so dugks_step needs no per-step upload;
+//   * otherwise: CTA b takes the (problem, tile) item work[b], and the
+//     problem's parity and step count come from its descriptor (advanced on
+//     the device by advance_kernel after each batched step).
+// Both uses run this same compiled code, so a problem's result does not
+// depend on whether, or with what, it is batched.
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct InstDesc {
+    CUtensorMap tm_state[2], tm_hist[2];  // 64-byte aligned maps of both ping-pong buffers
+    Real *state[2];
+    Real *hist[2];
+    unsigned *status;
+    Phys<Real> ph;
+    long long plane;
+    long long steps;                       // step count (batched use)
+    int nx, ny, pitch, tiles_x;
+    int cur;                               // buffer holding psi~^n (batched use)
+    int use_tma;
+};
+
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
+__global__ void __launch_bounds__(TX * TY, (TileShape<Real, TX, TY, COUPLED>::MINB))
+step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ work, int cur_override,
+            long long steps_override) {
+    const int2 item = work ? work[blockIdx.x] : make_int2(0, (int)blockIdx.x);   // (problem, tile)
+    const InstDesc<Real> *d = descs + item.x;
+    const int cur = work ? d->cur : cur_override;
+    const long long steps = work ? d->steps : steps_override;
+    StepArgs<Real> a;
+    a.src = d->state[cur];
+    a.dst = d->state[cur ^ 1];
+    a.hsrc = d->hist[cur];
+    a.hdst = d->hist[cur ^ 1];
+    a.nx = d->nx;
+    a.ny = d->ny;
+    a.pitch = d->pitch;
+    a.plane = d->plane;
+    a.first_step = steps == 0;
+    a.small = (a.nx < TX + 4 || a.ny < TY + 4) ? 1 : 0;
+    a.use_tma = d->use_tma;
+    a.status = d->status;
+    const Phys<Real> ph = d->ph;
+    const int tx = item.y % d->tiles_x, ty = item.y / d->tiles_x;
+    step_tile<Real, TX, TY, COUPLED, WALLY>(&d->tm_state[cur], &d->tm_hist[cur], a, ph, tx * TX, ty * TY);
+}
+
+// After a batched step: every instance's buffers swap and its step count grows.
+template <typename Real>
+__global__ void advance_kernel(InstDesc<Real> *descs, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        descs[i].cur ^= 1;
+        descs[i].steps += 1;
     }
 }
 

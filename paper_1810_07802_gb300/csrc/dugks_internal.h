@@ -2,18 +2,24 @@
 // per-precision kernel translation units.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <string.h>
 
+#include <cstring>
+
+#include "dugks.h"
 #include "dugks_device.cuh"
 
 namespace dugks {
 
 template <typename Real> struct FieldArgs;
+template <typename Real> struct InstDesc;
 
 template <typename Real>
-cudaError_t launch_step(const StepArgs<Real> &a, const Phys<Real> &ph, bool coupled, bool wally,
-                        const CUtensorMap *tm_state, const CUtensorMap *tm_hist, cudaStream_t st);
+cudaError_t launch_step(const InstDesc<Real> *desc, int nx, int ny, int cur, long long steps, bool coupled, bool wally,
+                        cudaStream_t st);
 template <typename Real>
 size_t step_smem_bytes(bool coupled);
 template <typename Real>
@@ -27,7 +33,85 @@ cudaError_t launch_macros(const FieldArgs<Real> &a, double *phid, const Phys<dou
 template <typename Real>
 cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, double p_ref, double *dist,
                           double *hist_out, cudaStream_t st);
+template <typename Real>
+cudaError_t batch_prepare(bool coupled, bool wally);
+template <typename Real>
+cudaError_t launch_batch_step(InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled, bool wally,
+                              cudaStream_t st);
 cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
                           int have_snap, double *partial, double *out, cudaStream_t st);
 
+
+// Workspace layout of one solver (offsets in bytes, 256-byte aligned regions).
+struct Layout {
+    int nq, pitch;
+    size_t elt, plane, n;
+    size_t off_state[2], off_hist[2], off_stage, off_phid, off_snap, off_partial, off_redout, off_status, off_desc;
+    size_t total;
+};
+
+}  // namespace dugks
+
+// The handle behind dugks_handle.
+struct dugks_ctx {
+    dugks_params P;
+    dugks::Layout L;
+    bool fp32, coupled, wally;
+    cudaStream_t st;
+    unsigned char *ws;
+    bool owns;
+    int cur;
+    int64_t steps;
+    int have_snap;
+    unsigned status_seen;
+    dugks::Phys<double> phd;
+    dugks::Phys<float> phf;
+    bool tma_ok;
+    CUtensorMap tm_state[2], tm_hist[2];
+
+    void *state(int b) const { return ws + L.off_state[b]; }
+    void *hist(int b) const { return ws + L.off_hist[b]; }
+    double *stage() const { return reinterpret_cast<double *>(ws + L.off_stage); }
+    double *phid() const { return reinterpret_cast<double *>(ws + L.off_phid); }
+    double *snap() const { return reinterpret_cast<double *>(ws + L.off_snap); }
+    double *partial() const { return reinterpret_cast<double *>(ws + L.off_partial); }
+    double *redout() const { return reinterpret_cast<double *>(ws + L.off_redout); }
+    unsigned *status() const { return reinterpret_cast<unsigned *>(ws + L.off_status); }
+    void *desc() const { return ws + L.off_desc; }
+
+    template <typename Real>
+    dugks::FieldArgs<Real> fields() const {
+        dugks::FieldArgs<Real> a;
+        a.state = static_cast<const Real *>(state(cur));
+        a.hist = static_cast<const Real *>(hist(cur));
+        a.nx = P.nx;
+        a.ny = P.ny;
+        a.pitch = L.pitch;
+        a.plane = (long long)L.plane;
+        return a;
+    }
+};
+
+namespace dugks {
+// Descriptor of one problem for the step kernel (device image built on the host).
+template <typename Real>
+inline void fill_desc(InstDesc<Real> *d, const dugks_ctx *c, const Phys<Real> &ph, int tx) {
+    std::memset(static_cast<void *>(d), 0, sizeof *d);
+    for (int b = 0; b < 2; b++) {
+        d->tm_state[b] = c->tm_state[b];
+        d->tm_hist[b] = c->tm_hist[b];
+        d->state[b] = static_cast<Real *>(c->state(b));
+        d->hist[b] = static_cast<Real *>(c->hist(b));
+    }
+    d->status = c->status();
+    d->ph = ph;
+    d->plane = (long long)c->L.plane;
+    d->steps = c->steps;
+    d->nx = c->P.nx;
+    d->ny = c->P.ny;
+    d->pitch = c->L.pitch;
+    d->tiles_x = (c->P.nx + tx - 1) / tx;
+    d->cur = c->cur;
+    d->use_tma = c->tma_ok ? 1 : 0;
+}
 }  // namespace dugks

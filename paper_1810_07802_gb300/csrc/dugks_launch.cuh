@@ -29,29 +29,52 @@ template <> struct Tile<double> { static constexpr int TX = DUGKS_TILE_F64_X, TY
 template <> struct Tile<float> { static constexpr int TX = DUGKS_TILE_F32_X, TY = DUGKS_TILE_F32_Y; };
 
 template <typename Real, bool COUPLED, bool WALLY>
-static cudaError_t launch_step_t(const StepArgs<Real> &a, const Phys<Real> &ph, const CUtensorMap *tm_state,
-                                 const CUtensorMap *tm_hist, cudaStream_t st) {
+static cudaError_t step_attr_t() {
     constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
     using S = TileShape<Real, TX, TY, COUPLED>;
-    auto kern = step_kernel<Real, TX, TY, COUPLED, WALLY>;
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
-    if (attr != cudaSuccess) return attr;
-    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-    StepArgs<Real> b = a;
-    b.small = (a.nx < TX + 4 || a.ny < TY + 4) ? 1 : 0;   // halo indices may wrap more than once
-    kern<<<grid, S::NT, S::smem_bytes, st>>>(*tm_state, *tm_hist, b, ph);
-    return cudaGetLastError();
+    static const cudaError_t attr = cudaFuncSetAttribute(step_kernel<Real, TX, TY, COUPLED, WALLY>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)S::smem_bytes);
+    return attr;
+}
+
+// Must run outside stream capture (sets the kernel's shared-memory limit).
+template <typename Real>
+cudaError_t step_prepare(bool coupled, bool wally) {
+    if (coupled) return wally ? step_attr_t<Real, true, true>() : step_attr_t<Real, true, false>();
+    return wally ? step_attr_t<Real, false, true>() : step_attr_t<Real, false, false>();
+}
+
+template <typename Real, bool COUPLED, bool WALLY>
+static void step_launch_t(const InstDesc<Real> *descs, const int2 *work, int nitems, int cur, long long steps,
+                          cudaStream_t st) {
+    constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
+    using S = TileShape<Real, TX, TY, COUPLED>;
+    step_kernel<Real, TX, TY, COUPLED, WALLY><<<nitems, S::NT, S::smem_bytes, st>>>(descs, work, cur, steps);
 }
 
 template <typename Real>
-cudaError_t launch_step(const StepArgs<Real> &a, const Phys<Real> &ph, bool coupled, bool wally,
-                        const CUtensorMap *tm_state, const CUtensorMap *tm_hist, cudaStream_t st) {
-    if (coupled)
-        return wally ? launch_step_t<Real, true, true>(a, ph, tm_state, tm_hist, st)
-                     : launch_step_t<Real, true, false>(a, ph, tm_state, tm_hist, st);
-    return wally ? launch_step_t<Real, false, true>(a, ph, tm_state, tm_hist, st)
-                 : launch_step_t<Real, false, false>(a, ph, tm_state, tm_hist, st);
+static void step_launch(const InstDesc<Real> *descs, const int2 *work, int nitems, int cur, long long steps,
+                        bool coupled, bool wally, cudaStream_t st) {
+    if (coupled) {
+        if (wally) step_launch_t<Real, true, true>(descs, work, nitems, cur, steps, st);
+        else step_launch_t<Real, true, false>(descs, work, nitems, cur, steps, st);
+    } else {
+        if (wally) step_launch_t<Real, false, true>(descs, work, nitems, cur, steps, st);
+        else step_launch_t<Real, false, false>(descs, work, nitems, cur, steps, st);
+    }
+}
+
+// One step of one problem whose descriptor is at desc (device memory).
+template <typename Real>
+cudaError_t launch_step(const InstDesc<Real> *desc, int nx, int ny, int cur, long long steps, bool coupled, bool wally,
+                        cudaStream_t st) {
+    cudaError_t e = step_prepare<Real>(coupled, wally);
+    if (e != cudaSuccess) return e;
+    constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
+    const int ntiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+    step_launch<Real>(desc, nullptr, ntiles, cur, steps, coupled, wally, st);
+    return cudaGetLastError();
 }
 
 template <typename Real>
@@ -62,6 +85,21 @@ size_t step_smem_bytes(bool coupled) {
 
 template <typename Real>
 int step_tile(int axis) { return axis == 0 ? Tile<Real>::TX : Tile<Real>::TY; }
+
+// ---- batched step ----
+template <typename Real>
+cudaError_t batch_prepare(bool coupled, bool wally) {
+    return step_prepare<Real>(coupled, wally);
+}
+
+template <typename Real>
+cudaError_t launch_batch_step(InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled, bool wally,
+                              cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    step_launch<Real>(descs, work, nwork, 0, 0, coupled, wally, st);
+    advance_kernel<Real><<<(ninst + 127) / 128, 128, 0, st>>>(descs, ninst);
+    return cudaGetLastError();
+}
 
 static inline dim3 cell_grid(int nx, int ny, int bx) { return dim3((nx + bx - 1) / bx, ny); }
 
@@ -105,8 +143,8 @@ cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, doub
 }
 
 #define DUGKS_INSTANTIATE(Real)                                                                                     \
-    template cudaError_t launch_step<Real>(const StepArgs<Real> &, const Phys<Real> &, bool, bool,                 \
-                                           const CUtensorMap *, const CUtensorMap *, cudaStream_t);                 \
+    template cudaError_t launch_step<Real>(const InstDesc<Real> *, int, int, int, long long, bool, bool,            \
+                                           cudaStream_t);                                                           \
     template size_t step_smem_bytes<Real>(bool);                                                                    \
     template int step_tile<Real>(int);                                                                              \
     template cudaError_t launch_init<Real>(const double *, Real *, Real *, int, int, int, long long,                \
@@ -114,6 +152,8 @@ cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, doub
     template cudaError_t launch_macros<Real>(const FieldArgs<Real> &, double *, const Phys<double> &, bool, bool,  \
                                              double *, double *, double *, double *, cudaStream_t);                 \
     template cudaError_t launch_export<Real>(const FieldArgs<Real> &, int, double, double, double *, double *,     \
-                                             cudaStream_t);
+                                             cudaStream_t);                                                        \
+    template cudaError_t batch_prepare<Real>(bool, bool);                                                          \
+    template cudaError_t launch_batch_step<Real>(InstDesc<Real> *, const int2 *, int, int, bool, bool, cudaStream_t);
 
 }  // namespace dugks

@@ -52,6 +52,13 @@ SIGNATURES = {
     "dugks_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dugks_reduce_fields_static": (ctypes.c_int, [_dp, _dp, _dp, _dp, ctypes.c_int64, _dp, ctypes.c_void_p]),
+    "dugks_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "dugks_batch_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "dugks_batch_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "dugks_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
+    "dugks_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "dugks_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "dugks_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 STATIC_REDUCE_MAX_CELLS = 16777216
@@ -265,3 +272,60 @@ class Solver:
     def set_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         _check(lib().dugks_set_state(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.size), "dugks_set_state")
+
+
+class Batch:
+    """Members (Solver objects) advanced together by dugks_batch_step."""
+
+    def __init__(self, stream=None):
+        import torch
+
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib().dugks_batch_create(ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+               "dugks_batch_create")
+        self.h = h
+        self.members = []
+
+    def add(self, solver):
+        _check(lib().dugks_batch_add(self.h, solver.h), "dugks_batch_add")
+        self.members.append(solver)
+
+    def remove(self, solver):
+        _check(lib().dugks_batch_remove(self.h, solver.h), "dugks_batch_remove")
+        self.members.remove(solver)
+
+    def __len__(self):
+        return int(lib().dugks_batch_size(self.h))
+
+    def step(self, n=1):
+        _check(lib().dugks_batch_step(self.h, int(n)), "dugks_batch_step")
+
+    def sync(self):
+        _check(lib().dugks_batch_sync(self.h), "dugks_batch_sync")
+
+    def mark(self):
+        """A torch event recorded after the work enqueued so far."""
+        import torch
+
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        return ev
+
+    def close(self):
+        if getattr(self, "h", None):
+            code = lib().dugks_batch_destroy(self.h)
+            self.h = None
+            _check(code, "dugks_batch_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -166,3 +166,35 @@ def random_state(nx, ny, seed=1, rho_ratio=1000.0, model="coupled", bc_y="period
                gravity_mode=1, gx=1e-6, gy=-2e-6, rho_ref=0.5 * (rho_ratio + 1.0),
                u0x=0.01, u0y=-0.007)
     return cfg, _fields(phi, ux, uy, p)
+
+
+def serving_trace(n=100, rate=50.0, seed=20181018, precision="fp32", burst=False,
+                  steps=None):
+    """A seeded stream of coupled solve requests shaped like the serving mix:
+    layered Poiseuille (mu* = 100, Nx = 4, Ny in {64..512}), stationary bubbles
+    (N in {64..512}, R = N/4, density ratio in {10, 100, 1000}) and spinodal
+    boxes (N in {128..1024}), with Poisson arrivals of mean `rate` per second
+    (all at t = 0 if burst).  Returns (kind, cfg, fields, steps, arrival)
+    tuples.  Step budgets per kind: Poiseuille 400, bubble 100, spinodal 200
+    (fixed budgets instead of a convergence test keep runs reproducible)."""
+    steps = steps or {"poiseuille": 400, "bubble": 100, "spinodal": 200}
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        kind = ("poiseuille", "bubble", "spinodal")[int(rng.integers(3))]
+        if kind == "poiseuille":
+            cfg, f = layered_poiseuille(ny=int(rng.choice([64, 128, 256, 512])), nx=4, mu_ratio=100.0, mu_h=1.0)
+        elif kind == "bubble":
+            N = int(rng.choice([64, 128, 256, 512]))
+            cfg, f = stationary_bubble(N=N, R=N / 4.0, rho_ratio=float(rng.choice([10.0, 100.0, 1000.0])))
+        else:
+            N = int(rng.choice([128, 256, 512, 1024]))
+            cfg, f = spinodal(N=N, seed=seed + i)
+        cfg["precision"] = precision
+        if precision == "fp32":
+            cfg.setdefault("phi_ref", 0.5)
+        if not burst:
+            t += float(rng.exponential(1.0 / rate))
+        out.append((kind, cfg, f, steps[kind], 0.0 if burst else t))
+    return out

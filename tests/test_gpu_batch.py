@@ -1,0 +1,114 @@
+"""Batches and the serving loop on the GPU: every problem's result in a batch
+(and in the continuous-batching server) is bit-identical to stepping it alone."""
+import numpy as np
+import pytest
+
+from paper_1810_07802_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1810_07802_gb300 import build, solver
+
+    build.build()
+    solver.lib()
+    return solver
+
+
+def problems():
+    out = []
+    cfg, f = W.random_state(150, 70, seed=1)
+    out.append((cfg, f))
+    cfg, f = W.random_state(37, 29, seed=2, bc_y="wall")
+    out.append((dict(cfg, precision="fp32", phi_ref=0.5), f))
+    cfg, f = W.stationary_bubble(N=64, R=16.0, rho_ratio=10.0)
+    out.append((dict(cfg, precision="fp32", phi_ref=0.5), f))
+    cfg, f = W.layered_poiseuille(ny=64, nx=4, mu_ratio=100.0)
+    out.append((cfg, f))
+    cfg, f = W.translation_circle(L=40, R=10.0, U=0.02)
+    out.append((cfg, f))
+    cfg, f = W.spinodal(N=96)
+    out.append((dict(cfg, precision="fp32"), f))
+    return out
+
+
+def alone(S, cfg, f, steps):
+    with S.Solver(cfg, **f) as s:
+        s.step(steps)
+        return s.macros(), s.get_state()
+
+
+def test_batch_bit_identical_to_alone(S):
+    import torch
+
+    probs = problems()
+    st = torch.cuda.Stream()
+    solvers = [S.Solver(c, stream=st, **f) for c, f in probs]
+    with S.Batch(stream=st) as b:
+        for s in solvers:
+            b.add(s)
+        assert len(b) == len(solvers)
+        b.step(3)
+        b.step(4)
+        b.sync()
+    for s, (c, f) in zip(solvers, probs):
+        assert s.step_count == 7
+        m, state = s.macros(), s.get_state()
+        m0, state0 = alone(S, c, f, 7)
+        for k in m:
+            assert np.array_equal(m[k], m0[k]), (c["nx"], c["ny"], k)
+        assert np.array_equal(state, state0)
+        s.close()
+
+
+def test_batch_membership_changes(S):
+    import torch
+
+    probs = problems()[:4]
+    st = torch.cuda.Stream()
+    solvers = [S.Solver(c, stream=st, **f) for c, f in probs]
+    with S.Batch(stream=st) as b:
+        b.add(solvers[0])
+        b.add(solvers[1])
+        b.step(2)
+        b.add(solvers[2])
+        b.step(3)
+        b.remove(solvers[0])
+        b.add(solvers[3])
+        b.step(4)
+        b.sync()
+    want = [5, 9, 7, 4]
+    for s, (c, f), n in zip(solvers, probs, want):
+        assert s.step_count == n
+        m0, _ = alone(S, c, f, n)
+        m = s.macros()
+        for k in m:
+            assert np.array_equal(m[k], m0[k])
+        s.close()
+
+
+def test_serving_results_identical_alone_and_in_the_mix(S):
+    from paper_1810_07802_gb300.serve import BatchingServer, Request, SequentialServer, summary
+
+    trace = W.serving_trace(n=10, rate=400.0, seed=5, steps={"poiseuille": 30, "bubble": 20, "spinodal": 15})
+    small = []
+    for i, (kind, cfg, f, steps, t) in enumerate(trace):
+        if cfg["nx"] * cfg["ny"] > 256 * 256:        # keep the test quick
+            cfg, f = W.spinodal(N=128, seed=99 + i)
+            cfg["precision"] = "fp32"
+        small.append(Request(i, kind, cfg, f, steps, t))
+    srv = BatchingServer(hbm_budget=8 << 30, max_members=6, chunk=8)
+    recs = srv.run(small)
+    assert len(recs) == len(small)
+    for r, q in zip(recs, small):
+        m0, _ = alone(S, q.cfg, q.fields, q.steps)
+        for k in m0:
+            assert np.array_equal(r.result[k], m0[k]), (q.rid, k)
+    s = summary(recs)
+    assert s["solves"] == len(small) and s["p99_ms"] >= s["p50_ms"] > 0
+    seq = SequentialServer().run(small)
+    for r, q in zip(seq, small):
+        for k in r.result:
+            assert np.array_equal(r.result[k], recs[q.rid].result[k])
