@@ -43,6 +43,11 @@
  *      adjacent cell's with the normal component removed (the mean of the
  *      cell and its mirror image), its lap phi is the adjacent cell's.
  *  R10 No clamping of phi, rho or mu.
+ *  R11 Prescribed velocity fields of the A-C-only model are evaluated
+ *      analytically: at cell centres at t_n = n dt, at face centres at
+ *      t_n + h (the time of the face distributions), with face coordinates
+ *      taken in [0, nx) x [0, ny) on periodic axes.  The reversing shear
+ *      (Eq. 42) changes sign for t >= L0/U0.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -198,6 +203,34 @@ void oracle_grad_lap(int nx, int ny, int wall_y, const double *phi,
         }
 }
 
+/* Prescribed velocity of the A-C-only model at (x, y), time t (R11). */
+static void prescribed_velocity(const oracle_params *P, double x, double y, double t, double *ux, double *uy)
+{
+    const double pi = 3.14159265358979323846;
+    double U = P->vel_u0, L = P->vel_length;
+    switch (P->velocity_field) {
+    case 1:  /* rotation about the box centre, Eq. 41 */
+        *ux = -U * pi / L * (y - 0.5 * L);
+        *uy = U * pi / L * (x - 0.5 * L);
+        break;
+    case 2: {  /* shear, reversed after L0 / U0, Eq. 42 */
+        double sgn = (t < L / U) ? 1.0 : -1.0;
+        *ux = sgn * U * pi * sin(pi * x / L) * cos(pi * y / L);
+        *uy = -sgn * U * pi * cos(pi * x / L) * sin(pi * y / L);
+        break;
+    }
+    case 3: {  /* smoothed deformation with period T = L0 / U0, Eq. 43 */
+        double c = cos(pi * t / (L / U));
+        *ux = -U * sin(4.0 * pi * x / L) * sin(4.0 * pi * y / L) * c;
+        *uy = -U * cos(4.0 * pi * x / L) * cos(4.0 * pi * y / L) * c;
+        break;
+    }
+    default:  /* uniform, Eq. 40 */
+        *ux = P->u0x;
+        *uy = P->u0y;
+    }
+}
+
 /* rho, grad rho, mu_phi, mu, tau_g, theta, n and F at a point whose phi,
  * grad phi and lap phi are set (Eqs. 3, 4, 6, 10, 34-36, R6, R8). */
 static void closures(const oracle_params *P, point_state *s)
@@ -281,8 +314,8 @@ static void cell_states(const oracle_ctx *c, point_state *cs)
             for (int i = 0; i < Q; i++) g9[i] = c->g[i * N + k];
             velocity_pressure(g9, 0.5 * dt, s);
         } else {
-            s->ux = P->u0x;
-            s->uy = P->u0y;
+            prescribed_velocity(P, (double)(k % nx) + 0.5, (double)(k / nx) + 0.5, (double)c->n * dt,
+                                &s->ux, &s->uy);
         }
         if (c->n == 0) {
             s->Dx = 0.0;
@@ -299,7 +332,7 @@ static void cell_states(const oracle_ctx *c, point_state *cs)
  * lap phi and d_t(phi u) (R3), then the original distributions (Eq. 28). */
 static void face_distributions(const oracle_ctx *c, const double *fbar, const double *gbar,
                                double dphix, double dphiy, double lap, double Dx, double Dy,
-                               int wall_face, double *fpsi, double *gpsi)
+                               int wall_face, double xf, double yf, double *fpsi, double *gpsi)
 {
     const oracle_params *P = &c->P;
     double dt = P->cfl, h = 0.5 * dt;
@@ -323,9 +356,11 @@ static void face_distributions(const oracle_ctx *c, const double *fbar, const do
             s.uy = 0.0;
             pressure(sum_nonrest, 0.5 * h, &s);
         }
+    } else if (wall_face) {
+        s.ux = 0.0;
+        s.uy = 0.0;
     } else {
-        s.ux = wall_face ? 0.0 : P->u0x;
-        s.uy = wall_face ? 0.0 : P->u0y;
+        prescribed_velocity(P, xf, yf, (double)c->n * dt + h, &s.ux, &s.uy);
     }
     double eq[Q], src[Q];
     oracle_feq(s.phi, s.ux, s.uy, eq);
@@ -460,7 +495,7 @@ static void one_step(oracle_ctx *c)
                                0.5 * (cs[kl].dphix + cs[kr].dphix), 0.5 * (cs[kl].dphiy + cs[kr].dphiy),
                                0.5 * (cs[kl].lap + cs[kr].lap),
                                0.5 * (cs[kl].Dx + cs[kr].Dx), 0.5 * (cs[kl].Dy + cs[kr].Dy),
-                               0, fp, gp);
+                               0, (double)((i + 1) % nx), (double)j + 0.5, fp, gp);
             for (int q = 0; q < Q; q++) { fxf[q * N + kl] = fp[q]; gxf[q * N + kl] = gp[q]; }
         }
 
@@ -476,7 +511,7 @@ static void one_step(oracle_ctx *c)
                 recon_wall(P, fbp, i, top, fb);
                 if (coupled) recon_wall(P, gbp, i, top, gb);
                 face_distributions(c, fb, gb, cs[k0].dphix, 0.0, cs[k0].lap, cs[k0].Dx, 0.0,
-                                   1, fp, gp);
+                                   1, (double)i + 0.5, (double)j, fp, gp);
             } else {
                 int jm = (j - 1 + ny) % ny, jc = j % ny;
                 long kd = (long)jm * nx + i, ku = (long)jc * nx + i;
@@ -486,7 +521,7 @@ static void one_step(oracle_ctx *c)
                                    0.5 * (cs[kd].dphix + cs[ku].dphix), 0.5 * (cs[kd].dphiy + cs[ku].dphiy),
                                    0.5 * (cs[kd].lap + cs[ku].lap),
                                    0.5 * (cs[kd].Dx + cs[ku].Dx), 0.5 * (cs[kd].Dy + cs[ku].Dy),
-                                   0, fp, gp);
+                                   0, (double)i + 0.5, (double)j, fp, gp);
             }
             for (int q = 0; q < Q; q++) { fyf[q * NF + kf] = fp[q]; gyf[q * NF + kf] = gp[q]; }
         }
@@ -526,6 +561,8 @@ static int params_valid(const oracle_params *P)
     if (P->nx < 3 || P->ny < 3) return 0;
     if (!(P->cfl > 0.0) || !(P->mobility > 0.0) || !(P->width > 0.0)) return 0;
     if (P->model != 0 && P->model != 1) return 0;
+    if (P->velocity_field < 0 || P->velocity_field > 3) return 0;
+    if (P->model == 1 && P->velocity_field > 0 && (!(P->vel_u0 > 0.0) || !(P->vel_length > 0.0))) return 0;
     if (P->model == 0) {
         if (!(P->rho_h > 0.0) || !(P->rho_l > 0.0)) return 0;
         if (!(P->mu_h > 0.0) || !(P->mu_l > 0.0)) return 0;
@@ -563,8 +600,7 @@ oracle_ctx *oracle_create(const oracle_params *p, const double *phi0,
             s.uy = uy0 ? uy0[k] : 0.0;
             s.p = p0 ? p0[k] : 0.0;
         } else {
-            s.ux = p->u0x;
-            s.uy = p->u0y;
+            prescribed_velocity(p, (double)(k % nx) + 0.5, (double)(k / nx) + 0.5, 0.0, &s.ux, &s.uy);
         }
         double eq[Q], src[Q];
         oracle_feq(s.phi, s.ux, s.uy, eq);             /* R7 */

@@ -39,7 +39,12 @@ typedef struct {
     double sigma;        /* surface tension (Eq. 3)                            */
     double gx, gy;       /* body force, see gravity_mode                      */
     double rho_ref;
-    double u0x, u0y;     /* prescribed velocity for model 1                    */
+    double u0x, u0y;     /* prescribed velocity for model 1, velocity_field 0  */
+    int velocity_field;  /* model 1: 0 uniform (u0x, u0y) (Eq. 40); 1 rotation (Eq. 41);
+                            2 reversing shear (Eq. 42); 3 smoothed deformation (Eq. 43) */
+    int reserved;
+    double vel_u0;       /* U0 of fields 1-3                                   */
+    double vel_length;   /* L0 of fields 1-3                                   */
 } oracle_params;
 
 typedef struct oracle_ctx oracle_ctx;

@@ -26,11 +26,14 @@ class OracleParams(ctypes.Structure):
         ("gx", ctypes.c_double), ("gy", ctypes.c_double),
         ("rho_ref", ctypes.c_double),
         ("u0x", ctypes.c_double), ("u0y", ctypes.c_double),
+        ("velocity_field", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("vel_u0", ctypes.c_double), ("vel_length", ctypes.c_double),
     ]
 
 
 _MODEL = {"coupled": 0, "ac": 1}
 _VISC = {"reciprocal": 0, "linear": 1}
+_FIELD = {"uniform": 0, "rotation": 1, "shear": 2, "deformation": 3}
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -83,8 +86,9 @@ def make_params(cfg):
     p.visc = _VISC[cfg.get("visc", "reciprocal")]
     p.gravity_mode = int(cfg.get("gravity_mode", 0))
     for k in ("cfl", "mobility", "width", "rho_h", "rho_l", "mu_h", "mu_l", "sigma",
-              "gx", "gy", "rho_ref", "u0x", "u0y"):
+              "gx", "gy", "rho_ref", "u0x", "u0y", "vel_u0", "vel_length"):
         setattr(p, k, float(cfg.get(k, 0.0)))
+    p.velocity_field = _FIELD[cfg.get("velocity_field", "uniform")]
     if cfg.get("bc_x", "periodic") != "periodic":
         raise ValueError("the oracle supports periodic x only")
     return p

@@ -66,6 +66,42 @@ def planar_slab(nx=64, ny=3, width=4.0, U=0.0, mobility=0.02, cfl=0.5, centre=No
     return cfg, _fields(_tanh_profile(d, width))
 
 
+def zalesak_disk(L=256, R=100.0, slot=20.0, U=0.02, mobility=0.02, width=4.0, cfl=0.5):
+    """Zalesak's slotted disk (Sec. III.B, Eq. 41): a disc of phi = 1 of radius R
+    centred in the L x L box with a vertical slot of the given width cut from
+    its bottom to 3/4 of its height (the paper's slot proportions are not
+    printed); sharp initial step.  One revolution takes T = 2 L / U0."""
+    X, Y = _centres(L, L)
+    c = L / 2.0
+    inside = np.hypot(X - c, Y - c) <= R
+    cut = (np.abs(X - c) <= slot / 2.0) & (Y <= c + 0.5 * R)
+    phi = np.where(inside & ~cut, 1.0, 0.0)
+    cfg = dict(nx=L, ny=L, model="ac", cfl=cfl, mobility=mobility, width=width,
+               velocity_field="rotation", vel_u0=U, vel_length=float(L))
+    return cfg, _fields(phi)
+
+
+def shear_elongation(L=256, U=0.02, mobility=0.01, width=4.0, cfl=0.5):
+    """Interface elongation in a reversing shear flow (Sec. III.C, Eq. 42): a
+    disc of radius L/5 at (0.5 L, 0.3 L); the field reverses after L0 / U0 and
+    the disc returns at T = 2 L0 / U0."""
+    X, Y = _centres(L, L)
+    r = np.hypot(X - 0.5 * L, Y - 0.3 * L)
+    cfg = dict(nx=L, ny=L, model="ac", cfl=cfl, mobility=mobility, width=width,
+               velocity_field="shear", vel_u0=U, vel_length=float(L))
+    return cfg, _fields(_tanh_profile(L / 5.0 - r, width))
+
+
+def smoothed_deformation(L=512, U=0.02, mobility=0.02, width=4.0, cfl=0.5):
+    """Deformation in a smoothed time-periodic shear flow (Sec. III.D, Eq. 43):
+    a centred disc of radius L/5, period T = L0 / U0."""
+    X, Y = _centres(L, L)
+    r = np.hypot(X - 0.5 * L, Y - 0.5 * L)
+    cfg = dict(nx=L, ny=L, model="ac", cfl=cfl, mobility=mobility, width=width,
+               velocity_field="deformation", vel_u0=U, vel_length=float(L))
+    return cfg, _fields(_tanh_profile(L / 5.0 - r, width))
+
+
 def stationary_bubble(N=128, R=32.0, width=4.0, rho_ratio=1000.0, nu=0.1, sigma=0.01,
                       mobility=0.02, cfl=0.5):
     """Light bubble (phi = 0) in heavy liquid, periodic N x N (Sec. IV.A, Eq. 45)."""

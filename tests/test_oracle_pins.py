@@ -363,3 +363,62 @@ def test_laplace_law():
     ratio = (P[N // 2, N // 2] - P[1, 1]) / (sigma / R)
     paper = GOLDEN["laplace_ratio"]["numerical_over_analytic"]
     assert abs(ratio - paper) < 0.09, ratio
+
+
+# ------------------------------------------- prescribed velocity fields (Sec. III)
+
+def _E(phi, ref):
+    return ((phi - ref) ** 2).sum() / (ref ** 2).sum()
+
+
+def test_zalesak_rotation_turns_the_disk():
+    """Sec. III.B (Eq. 41): the field rotates the box rigidly with period
+    2 L0 / U0, so after a quarter period the slotted disk's centroid has turned
+    by 90 degrees about the box centre, with phi mass conserved."""
+    L, U = 40, 0.04
+    cfg, f = W.zalesak_disk(L=L, R=15.0, slot=4.0, U=U)
+    o = O.Oracle(cfg, **f)
+    o.step(int(round(2 * L / U / 4 / cfg["cfl"])))
+    phi = o.macros()["phi"]
+    c = np.arange(L) + 0.5
+    X, Y = np.meshgrid(c, c)
+
+    def angle(p):
+        return math.degrees(math.atan2(((Y - L / 2) * p).sum(), ((X - L / 2) * p).sum()))
+
+    assert angle(f["phi0"]) == pytest.approx(90.0, abs=1e-9)
+    assert angle(phi) == pytest.approx(180.0, abs=2.0)
+    assert abs(phi.sum() - f["phi0"].sum()) < 1e-9 * f["phi0"].sum()
+
+
+@pytest.mark.slow
+def test_shear_elongation_is_reversed():
+    """Sec. III.C (Eq. 42): the disc is stretched for L0/U0 and the reversed
+    field brings it back; E (Eq. 39) at T is small (Table V magnitude) while
+    at T/2 the interface is far from its start."""
+    L, U = 32, 0.04
+    cfg, f = W.shear_elongation(L=L, U=U, width=2.0, mobility=0.01)
+    o = O.Oracle(cfg, **f)
+    n = int(round(2 * L / U / cfg["cfl"]))
+    o.step(n // 2)
+    mid = o.macros()["phi"]
+    o.step(n - n // 2)
+    end = o.macros()["phi"]
+    assert _E(mid, f["phi0"]) > 0.5
+    assert _E(end, f["phi0"]) < 2 * GOLDEN["table_V_shear_E_phi_vs_Pe"]["E"][0]
+    assert abs(end.sum() - f["phi0"].sum()) < 1e-12 * f["phi0"].sum() * n
+
+
+def test_smoothed_deformation_is_reversed():
+    """Sec. III.D (Eq. 43): the cos(pi t / T) factor reverses the deformation
+    in the second half period; the interface returns at T."""
+    L, U = 32, 0.04
+    cfg, f = W.smoothed_deformation(L=L, U=U, width=2.0)
+    o = O.Oracle(cfg, **f)
+    n = int(round(L / U / cfg["cfl"]))
+    o.step(n // 2)
+    mid = o.macros()["phi"]
+    o.step(n - n // 2)
+    end = o.macros()["phi"]
+    assert _E(end, f["phi0"]) < _E(mid, f["phi0"]) / 5
+    assert _E(end, f["phi0"]) < 0.1
