@@ -29,7 +29,7 @@ N_CELLS_SIDE = 2048
 FP32_BYTES_PER_CELL = 18 * 4 * 2 + 2 * 4 * 2   # read + write psi~ (18 FP32) and (phi u) history (2 FP32)
 FP64_BYTES_PER_CELL = 18 * 8 * 2 + 2 * 8 * 2
 REF_BAND_ROWS = 128
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_fp32_spinodal2048.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "solo_step_kernel_fp32_spinodal2048.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1810_07802_gb300", "csrc", f)
                   for f in ("dugks_device.cuh", "dugks_launch.cuh")]
 
@@ -309,7 +309,7 @@ def ours(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs, "unit": "GB/s",
                 "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": FP32_BYTES_PER_CELL * cells,
-                "peak_source": peak_src, "kernel": "step_kernel<float,32,8,coupled,periodic>"}
+                "peak_source": peak_src, "kernel": "solo_step_kernel<float,32,8,coupled,periodic>"}
 
     extra = {}
     if not args.no_fp64:

@@ -83,7 +83,15 @@ typedef struct {
     double gx, gy;         /* body force (see gravity_mode), coupled model only    */
     double rho_ref;        /* reference density for gravity_mode 1                 */
     double phi_ref, p_ref; /* rest state subtracted before FP32 storage            */
-    double u0x, u0y;       /* prescribed velocity of the Allen-Cahn-only model     */
+    double u0x, u0y;       /* uniform velocity of the Allen-Cahn-only model (Eq. 40) */
+    int32_t velocity_field; /* Allen-Cahn-only model: 0 uniform (u0x, u0y); 1 rotation
+                              about the box centre (Eq. 41); 2 shear reversed at
+                              t = L0/U0 (Eq. 42); 3 smoothed deformation with period
+                              L0/U0 (Eq. 43).  Evaluated at cell centres at t_n and
+                              at faces at t_n + dt/2                               */
+    int32_t reserved2;     /* must be 0                                            */
+    double vel_u0;         /* U0 > 0 of velocity fields 1-3                        */
+    double vel_length;     /* L0 > 0 of velocity fields 1-3                        */
 } dugks_params;
 
 typedef struct dugks_ctx *dugks_handle;

@@ -13,6 +13,7 @@ struct FieldArgs {
     const Real *__restrict__ hist;    // [2][ny][pitch]
     int nx, ny, pitch;
     long long plane;
+    double t;                         // time of the state (prescribed velocity fields)
 };
 
 // phi at cell (x, y) of a [ny][nx] double field, periodic in x, periodic or
@@ -54,8 +55,7 @@ __global__ void init_kernel(const double *__restrict__ in, Real *__restrict__ st
         s.uy = in[2 * N + c];
         s.pd = in[3 * N + c] - ph.p_ref;
     } else {
-        s.ux = ph.u0x;
-        s.uy = ph.u0y;
+        prescribed_velocity(ph, double(x) + 0.5, double(y) + 0.5, 0.0, s.ux, s.uy);
     }
     s.Dx = 0.0;
     s.Dy = 0.0;
@@ -111,8 +111,7 @@ __global__ void macro_kernel(FieldArgs<Real> a, const double *__restrict__ phid,
         }
         velocity_pressure(mx, my, sn, ph.half_dt, s);
     } else {
-        s.ux = ph.u0x;
-        s.uy = ph.u0y;
+        prescribed_velocity(ph, double(x) + 0.5, double(y) + 0.5, a.t, s.ux, s.uy);
         s.pd = 0.0;
     }
     if (ophi) ophi[c] = s.phi;

@@ -49,10 +49,13 @@ bool valid(const dugks_params *p) {
     if (p->bc_y != DUGKS_BC_PERIODIC && p->bc_y != DUGKS_BC_WALL) return false;
     if (p->visc_interp != DUGKS_VISC_RECIPROCAL && p->visc_interp != DUGKS_VISC_LINEAR) return false;
     if (p->gravity_mode != 0 && p->gravity_mode != 1) return false;
+    if (p->velocity_field < 0 || p->velocity_field > 3 || p->reserved2 != 0) return false;
     auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
     auto fin = [](double v) { return std::isfinite(v); };
     if (!pos(p->cfl) || !pos(p->mobility) || !pos(p->width)) return false;
     if (!fin(p->phi_ref) || !fin(p->p_ref) || !fin(p->u0x) || !fin(p->u0y)) return false;
+    if (p->model == DUGKS_AC_PRESCRIBED_U && p->velocity_field > 0 && (!pos(p->vel_u0) || !pos(p->vel_length)))
+        return false;
     if (p->model == DUGKS_COUPLED) {
         if (!pos(p->rho_h) || !pos(p->rho_l) || !pos(p->mu_h) || !pos(p->mu_l)) return false;
         if (!fin(p->sigma) || p->sigma < 0.0 || !fin(p->gx) || !fin(p->gy) || !fin(p->rho_ref)) return false;
@@ -84,7 +87,6 @@ Layout layout(const dugks_params *p) {
     L.off_partial = o; o = align_up(o + (size_t)dugks::RED_BLOCKS * dugks::RED_VALS * sizeof(double), kAlign);
     L.off_redout = o;  o = align_up(o + 8 * sizeof(double), kAlign);
     L.off_status = o;  o = align_up(o + sizeof(unsigned), kAlign);
-    L.off_desc = o;    o = align_up(o + std::max(sizeof(dugks::InstDesc<double>), sizeof(dugks::InstDesc<float>)), kAlign);
     L.total = o;
     return L;
 }
@@ -126,6 +128,13 @@ Phys<Real> make_phys(const dugks_params &p) {
     ph.p_ref = Real(p.p_ref);
     ph.u0x = Real(p.u0x);
     ph.u0y = Real(p.u0y);
+    ph.vel_kind = p.model == DUGKS_AC_PRESCRIBED_U ? p.velocity_field : 0;
+    if (ph.vel_kind > 0) {
+        ph.vel_u = Real(p.vel_u0);
+        ph.vel_il = Real(1.0 / p.vel_length);
+        ph.vel_ul = Real(p.vel_u0 / p.vel_length);
+        ph.vel_tr = p.vel_length / p.vel_u0;
+    }
     ph.visc_linear = p.visc_interp == DUGKS_VISC_LINEAR;
     ph.grav_mode = p.gravity_mode;
     return ph;
@@ -253,16 +262,7 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
                                                   L.pitch, 2, tx + 8, ty + 4);
         }
     }
-    // the step kernel's descriptor of this problem (buffers, constants, tensor maps)
-    std::vector<unsigned char> desc_img(std::max(sizeof(dugks::InstDesc<double>), sizeof(dugks::InstDesc<float>)));
-    if (c->fp32)
-        dugks::fill_desc(reinterpret_cast<dugks::InstDesc<float> *>(desc_img.data()), c, c->phf,
-                         dugks::step_tile<float>(0));
-    else
-        dugks::fill_desc(reinterpret_cast<dugks::InstDesc<double> *>(desc_img.data()), c, c->phd,
-                         dugks::step_tile<double>(0));
-    cudaError_t e = cudaMemcpyAsync(c->desc(), desc_img.data(), desc_img.size(), cudaMemcpyHostToDevice, c->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws, 0, L.off_stage, c->st);  // state, history (incl. row padding)
+    cudaError_t e = cudaMemsetAsync(c->ws, 0, L.off_stage, c->st);  // state, history (incl. row padding)
     const size_t fb = L.n * sizeof(double);
     double *in = c->stage();
     const double *src[4] = {phi0, ux0, uy0, p0};
@@ -298,11 +298,11 @@ dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
     for (int64_t n = 0; n < nsteps; n++) {
         cudaError_t e;
         if (c->fp32)
-            e = dugks::launch_step<float>(static_cast<const dugks::InstDesc<float> *>(c->desc()), c->P.nx, c->P.ny,
-                                          c->cur, c->steps, c->coupled, c->wally, c->st);
+            e = dugks::launch_step<float>(c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<float>(), c->phf,
+                                          c->coupled, c->wally, c->st);
         else
-            e = dugks::launch_step<double>(static_cast<const dugks::InstDesc<double> *>(c->desc()), c->P.nx,
-                                           c->P.ny, c->cur, c->steps, c->coupled, c->wally, c->st);
+            e = dugks::launch_step<double>(c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<double>(), c->phd,
+                                           c->coupled, c->wally, c->st);
         if (e != cudaSuccess) return from_cuda(e);
         c->cur ^= 1;
         c->steps++;

@@ -88,6 +88,9 @@ struct Phys {
     Real phi_ref, p_ref;
     Real u0x, u0y;
     int visc_linear, grav_mode;
+    int vel_kind;                 // prescribed field of the A-C-only model (0 uniform)
+    Real vel_u, vel_il, vel_ul;   // U0, 1/L0, U0/L0
+    double vel_tr;                // reversal time L0/U0 of the shear field
 };
 
 template <typename Real>
@@ -99,6 +102,7 @@ struct StepArgs {
     int nx, ny, pitch;
     long long plane;               // ny * pitch
     int first_step;
+    double t_n;                    // time at the start of the step
     int small;                     // grid smaller than a tile plus halo: wrap with %
     int use_tma;                   // tensor maps are valid: interior tiles load by TMA
     unsigned *status;
@@ -120,8 +124,42 @@ __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 // the FP64 path IEEE division.
 __device__ __forceinline__ float rcp_r(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sinpi_r(float x) { return sinpif(x); }
+__device__ __forceinline__ double sinpi_r(double x) { return sinpi(x); }
+__device__ __forceinline__ float cospi_r(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_r(double x) { return cospi(x); }
 __device__ __forceinline__ bool finite_r(float x) { return isfinite(x); }
 __device__ __forceinline__ bool finite_r(double x) { return isfinite(x); }
+
+// Prescribed velocity of the A-C-only model at (x, y), time t: uniform
+// (Eq. 40), rotation about the box centre (Eq. 41), shear reversed at
+// t = L0/U0 (Eq. 42), smoothed deformation with period L0/U0 (Eq. 43).
+template <typename Real>
+__device__ __forceinline__ void prescribed_velocity(const Phys<Real> &ph, Real x, Real y, double t, Real &ux,
+                                                    Real &uy) {
+    const Real pi = Real(3.14159265358979323846);
+    switch (ph.vel_kind) {
+    case 1:
+        ux = -ph.vel_u * pi * ph.vel_il * (y - Real(0.5) / ph.vel_il);
+        uy = ph.vel_u * pi * ph.vel_il * (x - Real(0.5) / ph.vel_il);
+        break;
+    case 2: {
+        const Real a = (t < ph.vel_tr ? Real(1) : Real(-1)) * ph.vel_u * pi;
+        ux = a * sinpi_r(x * ph.vel_il) * cospi_r(y * ph.vel_il);
+        uy = -a * cospi_r(x * ph.vel_il) * sinpi_r(y * ph.vel_il);
+        break;
+    }
+    case 3: {
+        const Real c = -ph.vel_u * cospi_r(Real(t) * ph.vel_ul);
+        ux = c * sinpi_r(Real(4) * x * ph.vel_il) * sinpi_r(Real(4) * y * ph.vel_il);
+        uy = c * cospi_r(Real(4) * x * ph.vel_il) * cospi_r(Real(4) * y * ph.vel_il);
+        break;
+    }
+    default:
+        ux = ph.u0x;
+        uy = ph.u0y;
+    }
+}
 
 // theta, n (Eq. 6) and, for the coupled model, rho, mu_phi, mu, tau_g and F
 // (Eqs. 3-4, 9-10, 34-36) from phi, grad phi and lap phi.
@@ -497,7 +535,8 @@ __device__ __forceinline__ void moments9(const Real g[9], Real &mx, Real &my, Re
 // in flux-slot order: out[slot] for f, out[6 + slot] for g.
 template <typename Real, bool COUPLED, bool XFACE>
 __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9], const Real gb[9], Real dpx,
-                                          Real dpy, Real lap, Real Dx, Real Dy, bool wall, Real out[12]) {
+                                          Real dpy, Real lap, Real Dx, Real Dy, bool wall, Real out[12], Real xf = Real(0),
+                                          Real yf = Real(0), double tf = 0.0) {
     Pt<Real> s;
     Real sphi = fb[0];
 #pragma unroll
@@ -519,9 +558,11 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
         } else {
             velocity_pressure(mx, my, sn, ph.half_h, s);
         }
+    } else if (wall) {
+        s.ux = Real(0);
+        s.uy = Real(0);
     } else {
-        s.ux = wall ? Real(0) : ph.u0x;
-        s.uy = wall ? Real(0) : ph.u0y;
+        prescribed_velocity(ph, xf, yf, tf, s.ux, s.uy);
     }
     const FLin<Real> lf = f_lin(ph, s, ph.ff_b, ph.ff_c);
 #pragma unroll
@@ -615,9 +656,13 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
         Real mx, my, sn;
         moments9(dg, mx, my, sn);
         velocity_pressure(mx, my, sn, ph.half_dt, s);
-    } else {
+    } else if (ph.vel_kind == 0) {
         s.ux = ph.u0x;
         s.uy = ph.u0y;
+    } else {
+        const int gx = a.small ? wrap(x0 + hx - 1, a.nx) : wrap1(x0 + hx - 1, a.nx);
+        const int gy = WALLY ? yraw : (a.small ? wrap(yraw, a.ny) : wrap1(yraw, a.ny));
+        prescribed_velocity(ph, Real(gx) + Real(0.5), Real(gy) + Real(0.5), a.t_n, s.ux, s.uy);
     }
     const Real phux = s.phi * s.ux, phuy = s.phi * s.uy;
     if (a.first_step) {
@@ -785,8 +830,10 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
             ady = S::F64 ? aux[L * AS + 4] : sdy[L];
             bdy = S::F64 ? aux[Rr * AS + 4] : sdy[Rr];
             const Real hf = Real(0.5);
+            const int gxf = x0 + fx >= nx ? x0 + fx - nx : x0 + fx;   // face coordinate in [0, nx)
             face_flux<Real, COUPLED, true>(ph, fb, gb, hf * (au[0] + bu[0]), hf * (au[1] + bu[1]), hf * (au[2] + bu[2]),
-                                           hf * (au[3] + bu[3]), hf * (ady + bdy), false, out);
+                                           hf * (au[3] + bu[3]), hf * (ady + bdy), false, out, Real(gxf),
+                                           Real(gyr) + Real(0.5), a.t_n + double(ph.h));
             store_flux<Real, COUPLED, FS>(sfx + t * FS, out);
         } else {
             const int u = t - S::NFX;
@@ -810,8 +857,10 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
                 ady = S::F64 ? aux[D * AS + 4] : sdy[D];
                 bdy = S::F64 ? aux[U * AS + 4] : sdy[U];
                 const Real hf = Real(0.5);
+                const int gyw = (!WALLY && gyf >= ny) ? gyf - ny : gyf;   // face coordinate in [0, ny)
                 face_flux<Real, COUPLED, false>(ph, fb, gb, hf * (au[0] + bu[0]), hf * (au[1] + bu[1]),
-                                                hf * (au[2] + bu[2]), hf * (au[3] + bu[3]), hf * (ady + bdy), false, out);
+                                                hf * (au[2] + bu[2]), hf * (au[3] + bu[3]), hf * (ady + bdy), false, out,
+                                                Real(x0 + fx) + Real(0.5), Real(gyw), a.t_n + double(ph.h));
             }
             store_flux<Real, COUPLED, FS>(sfy + u * FS, out);
         }
@@ -859,16 +908,12 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
 }
 
 // ---------------------------------------------------------------------------
-// The step kernel, for one problem or a batch of independent problems of the
-// same precision, model and y-boundary.  Each CTA runs one tile:
-//   * work == nullptr: one problem (descs[0]), CTA b takes tile b (x-major);
-//     its buffer parity and step count come from the launch (cur_override,
-//     steps_override), so dugks_step needs no per-step upload;
-//   * otherwise: CTA b takes the (problem, tile) item work[b], and the
-//     problem's parity and step count come from its descriptor (advanced on
-//     the device by advance_kernel after each batched step).
-// Both uses run this same compiled code, so a problem's result does not
-// depend on whether, or with what, it is batched.
+// The batched step kernel: a batch of independent problems of the same
+// precision, model and y-boundary.  CTA b runs the (problem, tile) item
+// work[b]; the problem's buffers, constants, tensor maps, buffer parity and
+// step count come from its descriptor (parity and count advanced on the
+// device by advance_kernel after each batched step).  solo_step_kernel below
+// runs the same tile code for one problem.
 // ---------------------------------------------------------------------------
 template <typename Real>
 struct InstDesc {
@@ -886,12 +931,11 @@ struct InstDesc {
 
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
 __global__ void __launch_bounds__(TX * TY, (TileShape<Real, TX, TY, COUPLED>::MINB))
-step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ work, int cur_override,
-            long long steps_override) {
-    const int2 item = work ? work[blockIdx.x] : make_int2(0, (int)blockIdx.x);   // (problem, tile)
+step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ work) {
+    const int2 item = work[blockIdx.x];   // (problem, tile)
     const InstDesc<Real> *d = descs + item.x;
-    const int cur = work ? d->cur : cur_override;
-    const long long steps = work ? d->steps : steps_override;
+    const int cur = d->cur;
+    const long long steps = d->steps;
     StepArgs<Real> a;
     a.src = d->state[cur];
     a.dst = d->state[cur ^ 1];
@@ -902,12 +946,26 @@ step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ w
     a.pitch = d->pitch;
     a.plane = d->plane;
     a.first_step = steps == 0;
+    a.t_n = double(steps) * double(d->ph.dt);
     a.small = (a.nx < TX + 4 || a.ny < TY + 4) ? 1 : 0;
     a.use_tma = d->use_tma;
     a.status = d->status;
-    const Phys<Real> ph = d->ph;
+    const Phys<Real> &ph = d->ph;   // read-only: reloaded on demand rather than pinned in registers
     const int tx = item.y % d->tiles_x, ty = item.y / d->tiles_x;
     step_tile<Real, TX, TY, COUPLED, WALLY>(&d->tm_state[cur], &d->tm_hist[cur], a, ph, tx * TX, ty * TY);
+}
+
+// One step of a single problem.  Tensor maps, arguments and constants arrive
+// in the kernel's parameter space, which the arithmetic instructions read as
+// constant-bank operands without occupying registers; the tile code is the
+// same inlined function the batched kernel runs, so a problem gives the same
+// bits stepped alone or in a batch.
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
+__global__ void __launch_bounds__(TX * TY)
+solo_step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_constant__ CUtensorMap tm_hist,
+                 const __grid_constant__ StepArgs<Real> a, const __grid_constant__ Phys<Real> ph, int tiles_x) {
+    const int tile = (int)blockIdx.x;
+    step_tile<Real, TX, TY, COUPLED, WALLY>(&tm_state, &tm_hist, a, ph, (tile % tiles_x) * TX, (tile / tiles_x) * TY);
 }
 
 // After a batched step: every instance's buffers swap and its step count grows.

@@ -18,8 +18,8 @@ template <typename Real> struct FieldArgs;
 template <typename Real> struct InstDesc;
 
 template <typename Real>
-cudaError_t launch_step(const InstDesc<Real> *desc, int nx, int ny, int cur, long long steps, bool coupled, bool wally,
-                        cudaStream_t st);
+cudaError_t launch_step(const CUtensorMap &tm_state, const CUtensorMap &tm_hist, const StepArgs<Real> &a,
+                        const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st);
 template <typename Real>
 size_t step_smem_bytes(bool coupled);
 template <typename Real>
@@ -46,7 +46,7 @@ cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy,
 struct Layout {
     int nq, pitch;
     size_t elt, plane, n;
-    size_t off_state[2], off_hist[2], off_stage, off_phid, off_snap, off_partial, off_redout, off_status, off_desc;
+    size_t off_state[2], off_hist[2], off_stage, off_phid, off_snap, off_partial, off_redout, off_status;
     size_t total;
 };
 
@@ -77,7 +77,27 @@ struct dugks_ctx {
     double *partial() const { return reinterpret_cast<double *>(ws + L.off_partial); }
     double *redout() const { return reinterpret_cast<double *>(ws + L.off_redout); }
     unsigned *status() const { return reinterpret_cast<unsigned *>(ws + L.off_status); }
-    void *desc() const { return ws + L.off_desc; }
+
+    // Arguments of the next step (psi~^n in buffer cur).
+    template <typename Real>
+    dugks::StepArgs<Real> step_args() const {
+        const int tx = dugks::step_tile<Real>(0), ty = dugks::step_tile<Real>(1);
+        dugks::StepArgs<Real> a;
+        a.src = static_cast<const Real *>(state(cur));
+        a.dst = static_cast<Real *>(state(cur ^ 1));
+        a.hsrc = static_cast<const Real *>(hist(cur));
+        a.hdst = static_cast<Real *>(hist(cur ^ 1));
+        a.nx = P.nx;
+        a.ny = P.ny;
+        a.pitch = L.pitch;
+        a.plane = (long long)L.plane;
+        a.first_step = steps == 0;
+        a.t_n = double(steps) * double(fp32 ? (double)phf.dt : phd.dt);
+        a.small = (P.nx < tx + 4 || P.ny < ty + 4) ? 1 : 0;
+        a.use_tma = tma_ok ? 1 : 0;
+        a.status = status();
+        return a;
+    }
 
     template <typename Real>
     dugks::FieldArgs<Real> fields() const {
@@ -88,6 +108,7 @@ struct dugks_ctx {
         a.ny = P.ny;
         a.pitch = L.pitch;
         a.plane = (long long)L.plane;
+        a.t = double(steps) * P.cfl;
         return a;
     }
 };

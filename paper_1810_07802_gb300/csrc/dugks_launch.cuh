@@ -35,7 +35,10 @@ static cudaError_t step_attr_t() {
     static const cudaError_t attr = cudaFuncSetAttribute(step_kernel<Real, TX, TY, COUPLED, WALLY>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)S::smem_bytes);
-    return attr;
+    static const cudaError_t attr_solo = cudaFuncSetAttribute(solo_step_kernel<Real, TX, TY, COUPLED, WALLY>,
+                                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                              (int)S::smem_bytes);
+    return attr != cudaSuccess ? attr : attr_solo;
 }
 
 // Must run outside stream capture (sets the kernel's shared-memory limit).
@@ -46,34 +49,30 @@ cudaError_t step_prepare(bool coupled, bool wally) {
 }
 
 template <typename Real, bool COUPLED, bool WALLY>
-static void step_launch_t(const InstDesc<Real> *descs, const int2 *work, int nitems, int cur, long long steps,
-                          cudaStream_t st) {
+static void batch_launch_t(const InstDesc<Real> *descs, const int2 *work, int nitems, cudaStream_t st) {
     constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
     using S = TileShape<Real, TX, TY, COUPLED>;
-    step_kernel<Real, TX, TY, COUPLED, WALLY><<<nitems, S::NT, S::smem_bytes, st>>>(descs, work, cur, steps);
+    step_kernel<Real, TX, TY, COUPLED, WALLY><<<nitems, S::NT, S::smem_bytes, st>>>(descs, work);
 }
 
+// One step of one problem: maps, arguments and constants by value.
 template <typename Real>
-static void step_launch(const InstDesc<Real> *descs, const int2 *work, int nitems, int cur, long long steps,
-                        bool coupled, bool wally, cudaStream_t st) {
-    if (coupled) {
-        if (wally) step_launch_t<Real, true, true>(descs, work, nitems, cur, steps, st);
-        else step_launch_t<Real, true, false>(descs, work, nitems, cur, steps, st);
-    } else {
-        if (wally) step_launch_t<Real, false, true>(descs, work, nitems, cur, steps, st);
-        else step_launch_t<Real, false, false>(descs, work, nitems, cur, steps, st);
-    }
-}
-
-// One step of one problem whose descriptor is at desc (device memory).
-template <typename Real>
-cudaError_t launch_step(const InstDesc<Real> *desc, int nx, int ny, int cur, long long steps, bool coupled, bool wally,
-                        cudaStream_t st) {
+cudaError_t launch_step(const CUtensorMap &tm_state, const CUtensorMap &tm_hist, const StepArgs<Real> &a,
+                        const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st) {
     cudaError_t e = step_prepare<Real>(coupled, wally);
     if (e != cudaSuccess) return e;
     constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
-    const int ntiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
-    step_launch<Real>(desc, nullptr, ntiles, cur, steps, coupled, wally, st);
+    const int tiles_x = (a.nx + TX - 1) / TX;
+    const int ntiles = tiles_x * ((a.ny + TY - 1) / TY);
+    if (coupled) {
+        using S = TileShape<Real, TX, TY, true>;
+        if (wally) solo_step_kernel<Real, TX, TY, true, true><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph, tiles_x);
+        else solo_step_kernel<Real, TX, TY, true, false><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph, tiles_x);
+    } else {
+        using S = TileShape<Real, TX, TY, false>;
+        if (wally) solo_step_kernel<Real, TX, TY, false, true><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph, tiles_x);
+        else solo_step_kernel<Real, TX, TY, false, false><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph, tiles_x);
+    }
     return cudaGetLastError();
 }
 
@@ -96,7 +95,13 @@ template <typename Real>
 cudaError_t launch_batch_step(InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled, bool wally,
                               cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
-    step_launch<Real>(descs, work, nwork, 0, 0, coupled, wally, st);
+    if (coupled) {
+        if (wally) batch_launch_t<Real, true, true>(descs, work, nwork, st);
+        else batch_launch_t<Real, true, false>(descs, work, nwork, st);
+    } else {
+        if (wally) batch_launch_t<Real, false, true>(descs, work, nwork, st);
+        else batch_launch_t<Real, false, false>(descs, work, nwork, st);
+    }
     advance_kernel<Real><<<(ninst + 127) / 128, 128, 0, st>>>(descs, ninst);
     return cudaGetLastError();
 }
@@ -143,8 +148,8 @@ cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, doub
 }
 
 #define DUGKS_INSTANTIATE(Real)                                                                                     \
-    template cudaError_t launch_step<Real>(const InstDesc<Real> *, int, int, int, long long, bool, bool,            \
-                                           cudaStream_t);                                                           \
+    template cudaError_t launch_step<Real>(const CUtensorMap &, const CUtensorMap &, const StepArgs<Real> &,       \
+                                           const Phys<Real> &, bool, bool, cudaStream_t);                          \
     template size_t step_smem_bytes<Real>(bool);                                                                    \
     template int step_tile<Real>(int);                                                                              \
     template cudaError_t launch_init<Real>(const double *, Real *, Real *, int, int, int, long long,                \

@@ -28,6 +28,8 @@ class DugksParams(ctypes.Structure):
         ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("rho_ref", ctypes.c_double),
         ("phi_ref", ctypes.c_double), ("p_ref", ctypes.c_double),
         ("u0x", ctypes.c_double), ("u0y", ctypes.c_double),
+        ("velocity_field", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("vel_u0", ctypes.c_double), ("vel_length", ctypes.c_double),
     ]
 
 
@@ -106,6 +108,7 @@ _ENUM = {
     "precision": {"fp64": 0, "fp32": 1},
     "bc": {"periodic": 0, "wall": 1},
     "visc": {"reciprocal": 0, "linear": 1},
+    "velocity_field": {"uniform": 0, "rotation": 1, "shear": 2, "deformation": 3},
 }
 
 
@@ -121,8 +124,10 @@ def make_params(cfg):
     p.gravity_mode = int(cfg.get("gravity_mode", 0))
     p.reserved = 0
     for k in ("cfl", "mobility", "width", "rho_h", "rho_l", "mu_h", "mu_l", "sigma", "gx", "gy",
-              "rho_ref", "phi_ref", "p_ref", "u0x", "u0y"):
+              "rho_ref", "phi_ref", "p_ref", "u0x", "u0y", "vel_u0", "vel_length"):
         setattr(p, k, float(cfg.get(k, 0.0)))
+    p.velocity_field = _ENUM["velocity_field"][cfg.get("velocity_field", "uniform")]
+    p.reserved2 = 0
     if p.precision == 0:
         # the FP64 path keeps absolute distributions unless asked otherwise
         p.phi_ref = float(cfg.get("phi_ref_fp64", 0.0))

@@ -34,8 +34,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_params_struct_size_matches_header():
-    # 10 int32 fields followed by 15 doubles, no padding
-    assert ctypes.sizeof(solver.DugksParams) == 10 * 4 + 15 * 8
+    # 10 int32 fields, 15 doubles, 2 int32 (velocity field, reserved), 2 doubles; no padding
+    assert ctypes.sizeof(solver.DugksParams) == 10 * 4 + 15 * 8 + 2 * 4 + 2 * 8
 
 
 def test_workspace_bytes_and_validation(lib):

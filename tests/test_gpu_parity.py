@@ -101,6 +101,35 @@ def test_allen_cahn_only_fp64(S, bc_y):
     assert_parity(got, ref, dist, st, what="A-C " + bc_y)
 
 
+@pytest.mark.parametrize("name,steps", [("rotation", 40), ("shear", 30), ("deformation", 30),
+                                        ("shear_reversal", 420)])
+def test_prescribed_velocity_fields_fp64(S, name, steps):
+    """A-C-only model with the paper's rotation (Eq. 41), reversing shear (Eq. 42)
+    and smoothed deformation (Eq. 43) fields, including a run across the shear's
+    reversal time."""
+    if name == "rotation":
+        cfg, f = W.zalesak_disk(L=40, R=15.0, slot=4.0, U=0.04)
+    elif name == "shear":
+        cfg, f = W.shear_elongation(L=48, U=0.04)
+    elif name == "deformation":
+        cfg, f = W.smoothed_deformation(L=64, U=0.04)
+    else:
+        cfg, f = W.shear_elongation(L=16, U=0.08, width=2.0)
+    got, ref, dist, st = run_both(S, cfg, f, steps)
+    assert_parity(got, ref, dist, st, what=name)
+
+
+def test_prescribed_velocity_fp32(S):
+    cfg, f = W.smoothed_deformation(L=96, U=0.04)
+    with S.Solver(dict(cfg, precision="fp32"), **f) as s:
+        s.step(30)
+        got = s.macros()
+    o = Oracle(cfg, **f)
+    o.step(30)
+    ref = o.macros()
+    assert np.abs(got["phi"] - ref["phi"]).max() <= 2e-5
+
+
 def test_paper_workloads_fp64(S):
     """Reduced-size versions of the paper's problems: bubble, Poiseuille, RTI."""
     cases = [W.stationary_bubble(N=48, R=12.0, rho_ratio=1000.0),
