@@ -356,10 +356,26 @@ __device__ __forceinline__ void ld2(const double *p, double o[2]) {
 __device__ __forceinline__ void st2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
 __device__ __forceinline__ void st2(double *p, double a, double b) { *reinterpret_cast<double2 *>(p) = make_double2(a, b); }
 
+// Warps per CTA beyond one thread per tile cell.  They take halo-ring cells
+// in phase 2 and their share of faces in phase 3, which shortens the phase
+// tails (FP32 32 x 8: the 84 ring cells run beside the 256 tile cells, the
+// 552 faces take 2 rounds of 320 threads instead of 3 of 256) at the cost of
+// idling in the flux update.  Measured on GB300 (2048^2 spinodal, FP32):
+// 0.353 / 0.343 / 0.333 / 0.350 / 0.345 ms per step for 0 / 1 / 2 / 3 / 4
+// extra warps (3 CTAs per SM, registers capped to fit); FP64 16 x 8: 10.40 /
+// 10.38 / 10.22 ms for 0 / 1 / 2.
+#ifndef DUGKS_EXTRA_WARPS_F32
+#define DUGKS_EXTRA_WARPS_F32 2
+#endif
+#ifndef DUGKS_EXTRA_WARPS_F64
+#define DUGKS_EXTRA_WARPS_F64 2
+#endif
+
 template <typename Real, int TX, int TY, bool COUPLED>
 struct TileShape {
     static constexpr bool F64 = sizeof(Real) == 8;
-    static constexpr int NT = TX * TY;
+    static constexpr int NC = TX * TY;                                            // tile cells
+    static constexpr int NT = NC + 32 * (F64 ? DUGKS_EXTRA_WARPS_F64 : DUGKS_EXTRA_WARPS_F32);  // threads
     static constexpr int HX2 = TX + 4, HY2 = TY + 4;  // phi region (halo 2)
     static constexpr int HX1 = TX + 2, HY1 = TY + 2;  // psi-bar-plus region (halo 1)
     static constexpr int N2 = HX2 * HY2, N1 = HX1 * HY1;
@@ -369,6 +385,10 @@ struct TileShape {
     // planes followed by the 2 history planes.
     static constexpr int BX = TX + 8, BY = TY + 4, BXY = BX * BY;
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+#ifndef DUGKS_FACE_PAD
+#define DUGKS_FACE_PAD 1
+#endif
+    static constexpr int NFXP = DUGKS_FACE_PAD ? (NFX + 31) / 32 * 32 : NFX;   // x-face items, padded
     static constexpr int NFD = COUPLED ? 12 : 6;                               // flux values per face
     static constexpr int RS = Rec<COUPLED>::NG * 4 + (F64 ? 2 : 0);            // record stride
     static constexpr int AS = F64 ? 6 : 4;                                     // aux stride (FP32: d_t(phi u)_y apart)
@@ -798,12 +818,14 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     }
     __syncthreads();
 
-    // 2. the tile cell of this thread, then at most one halo-ring cell
+    // 2. items t < NC are the tile cells (their psi~+ partials stay in the
+    //    registers of threads 0..NC-1), items t >= NC the halo ring
     Real tp[18];
-    cell_item<Real, TX, TY, COUPLED, WALLY, true>(a, ph, box, sphi, rec, aux, sdy, tid % TX + 1, tid / TX + 1, x0,
-                                                  y0, tp);
-    for (int t = tid + S::NT; t < S::N1; t += S::NT) {
-        const int r = t - S::NT;
+    if (tid < S::NC)
+        cell_item<Real, TX, TY, COUPLED, WALLY, true>(a, ph, box, sphi, rec, aux, sdy, tid % TX + 1, tid / TX + 1,
+                                                      x0, y0, tp);
+    for (int t = tid < S::NC ? tid + S::NT : tid; t < S::N1; t += S::NT) {
+        const int r = t - S::NC;
         int hx, hy;
         if (r < S::HX1) { hx = r; hy = 0; }
         else if (r < 2 * S::HX1) { hx = r - S::HX1; hy = S::HY1 - 1; }
@@ -814,10 +836,13 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     __syncthreads();
 
     // 3. faces: x-faces (west face of local cell (fx, fy)), then y-faces (south face)
-    for (int t = tid; t < S::NFX + S::NFY; t += S::NT) {
+    //    (the y-face items start on a warp boundary, so no warp mixes both
+    //    kinds: 0.333 -> 0.324 ms per FP32 2048^2 step on GB300)
+    for (int t = tid; t < S::NFXP + S::NFY; t += S::NT) {
         Real fb[9], gb[9], out[12];
         Real au[4], bu[4], ady, bdy;
-        if (t < S::NFX) {
+        if (t < S::NFXP) {
+            if (t >= S::NFX) continue;
             const int fx = t % (TX + 1), fy = t / (TX + 1);
             const int gyr = y0 + fy;
             if (gyr >= ny || x0 + fx - 1 >= nx) continue;
@@ -836,7 +861,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
                                            Real(gyr) + Real(0.5), a.t_n + double(ph.h));
             store_flux<Real, COUPLED, FS>(sfx + t * FS, out);
         } else {
-            const int u = t - S::NFX;
+            const int u = t - S::NFXP;
             const int fx = u % TX, fy = u / TX;
             const int gyf = y0 + fy;  // face below row gyf
             if (x0 + fx >= nx || gyf - 1 >= ny) continue;
@@ -868,7 +893,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     __syncthreads();
 
     // 4. the flux update of the tile
-    {
+    if (tid < S::NC) {
         const int lx = tid % TX, ly = tid / TX;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx < nx && gy < ny) {
@@ -930,7 +955,7 @@ struct InstDesc {
 };
 
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
-__global__ void __launch_bounds__(TX * TY, (TileShape<Real, TX, TY, COUPLED>::MINB))
+__global__ void __launch_bounds__((TileShape<Real, TX, TY, COUPLED>::NT), (TileShape<Real, TX, TY, COUPLED>::MINB))
 step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ work) {
     const int2 item = work[blockIdx.x];   // (problem, tile)
     const InstDesc<Real> *d = descs + item.x;
@@ -960,8 +985,12 @@ step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ w
 // constant-bank operands without occupying registers; the tile code is the
 // same inlined function the batched kernel runs, so a problem gives the same
 // bits stepped alone or in a batch.
+#ifndef DUGKS_SOLO_MINB
+#define DUGKS_SOLO_MINB 0   // 0: the occupancy the shared memory allows
+#endif
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__((TileShape<Real, TX, TY, COUPLED>::NT),
+                                  (DUGKS_SOLO_MINB > 0 ? DUGKS_SOLO_MINB : TileShape<Real, TX, TY, COUPLED>::MINB))
 solo_step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_constant__ CUtensorMap tm_hist,
                  const __grid_constant__ StepArgs<Real> a, const __grid_constant__ Phys<Real> ph, int tiles_x) {
     const int tile = (int)blockIdx.x;
