@@ -69,6 +69,21 @@ def config_dict(precision):
 
 # ------------------------------------------------------------------ helpers
 
+def job_time_and_value(local_secs, units_per_rank, world, device="cuda"):
+    """Whole-job timing of independent replicas: the slowest rank's time and
+    the units all ranks processed divided by it (weak scaling, no data-path
+    collective; the one all-reduce carries the timings)."""
+    secs = float(local_secs)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([secs], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    return secs, units_per_rank * world / secs
+
+
 def dist_setup(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -189,10 +204,7 @@ def run_gpu_measure(precision, steps, warmup, world, rank):
     torch.cuda.synchronize()
     secs = time_steps(s, stream, steps)
     s.sync()   # raises if the device status word reports a non-finite or non-physical step
-    if world > 1:
-        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+    secs, _ = job_time_and_value(secs, 1, world)
     s.close()
     return secs, cfg
 
@@ -298,8 +310,7 @@ def ours(args):
         secs, cfg = run_gpu_measure("fp32", args.steps, args.warmup, world, rank)
     clocks = clk.summary()
     cells = cfg["nx"] * cfg["ny"]
-    mlups_rank = cells * args.steps / secs / 1e6
-    value = mlups_rank * world
+    value = cells * args.steps * world / secs / 1e6   # secs: the slowest rank's
     ms_step = secs / args.steps * 1e3
 
     peaks = measured_peaks()
