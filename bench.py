@@ -251,7 +251,7 @@ def run_serving(n=100, rate=50.0):
     arrivals): continuous batching (FP32-shifted) against one solve at a time
     (FP32 and FP64), and the same requests as one burst."""
     from paper_1810_07802_gb300 import workloads as W
-    from paper_1810_07802_gb300.serve import BatchingServer, Request, SequentialServer, summary
+    from paper_1810_07802_gb300.serve import AutotuneCache, BatchingServer, Request, SequentialServer, summary
 
     def requests(precision, burst):
         tr = W.serving_trace(n=n, rate=rate, precision=precision, burst=burst)
@@ -267,12 +267,24 @@ def run_serving(n=100, rate=50.0):
     out = {"workload": "%d requests: layered Poiseuille (Ny 64-512, Nx 4, 400 steps), stationary bubbles "
                        "(N 64-512, ratio 10/100/1000, 100 steps), spinodal boxes (N 128-1024, 200 steps)" % n,
            "hbm_budget_bytes": budget}
+    tuner = AutotuneCache(trial_steps=10)   # shapes are tuned before a run's clock starts
+    t_tune = 0.0
     for label, burst in (("poisson_%g_per_s" % rate, False), ("burst", True)):
         r32, r64 = requests("fp32", burst), requests("fp64", burst)
         out[label] = {"batched_fp32": keep(summary(BatchingServer(budget, max_members=128, chunk=50,
                                                                   keep_results=False).run(r32))),
                       "sequential_fp32": keep(summary(SequentialServer(keep_results=False).run(r32))),
                       "sequential_fp64": keep(summary(SequentialServer(keep_results=False).run(r64)))}
+        t0 = time.perf_counter()
+        for r in requests("fp32", burst):
+            tuner(r.cfg, r.fields)
+        t_tune += time.perf_counter() - t0
+        out[label]["batched_fp32_autotuned"] = keep(summary(BatchingServer(
+            budget, max_members=128, chunk=50, keep_results=False, tile_policy=tuner).run(requests("fp32", burst))))
+    chosen = {}
+    for k, v in tuner.shapes.items():
+        chosen["%s %dx%d" % (k[1], k[3], k[4])] = v
+    out["autotune"] = {"shapes_tuned": len(tuner.shapes), "tuning_s": round(t_tune, 3), "tile_shape": chosen}
     return out
 
 

@@ -73,7 +73,10 @@ typedef struct {
     int32_t bc_y;          /* periodic, or no-slip walls on y = 0 and y = ny       */
     int32_t visc_interp;   /* dugks_visc: 1/mu linear in phi (Eq. 35) or mu (Eq. 36) */
     int32_t gravity_mode;  /* 0: G = (gx, gy); 1: G = (rho - rho_ref)(gx, gy)      */
-    int32_t reserved;      /* must be 0                                            */
+    int32_t tile_shape;    /* step-kernel tile: 0 the library default, k >= 1 the
+                              k-th compiled shape of the precision (see
+                              dugks_tile_shapes, dugks_autotune).  Every shape
+                              computes the same scheme                             */
     double cfl;            /* dt = cfl (Eq. 37 with delta_x = 1, RT = 1/3), > 0    */
     double mobility;       /* M_phi > 0; tau_f = M_phi / RT (Eq. 34)               */
     double width;          /* interface width W > 0 (Eq. 3)                        */
@@ -100,6 +103,26 @@ typedef struct dugks_ctx *dugks_handle;
  * buffers, macro staging, reduction scratch), or 0 if the parameters are
  * invalid.  Used for admission by HBM footprint. */
 size_t dugks_workspace_bytes(const dugks_params *params);
+
+/* Tile shapes the step kernels are compiled for, for one precision: writes
+ * up to `cap` (tx, ty) cell counts (tx may be NULL, likewise ty) and returns
+ * how many there are (tile_shape k >= 1 selects entry k - 1), or -1 for an
+ * unknown precision.  Shape 1 is the library default.  No device work. */
+int32_t dugks_tile_shapes(int32_t precision, int32_t *tx, int32_t *ty, int32_t cap);
+
+/* Autotuner of the step kernel's tile shape for one problem.  For every
+ * compiled shape it creates the problem (params, with tile_shape replaced,
+ * and the host fields as for dugks_create) in a library-allocated workspace,
+ * runs 2 warm-up steps, times trial_steps (>= 1) steps with CUDA events on
+ * cuda_stream and destroys it; one shape at a time, so the device memory
+ * needed is one workspace.  Writes the fastest tile_shape value (>= 1) to
+ * *best and, if ms_per_step is not NULL, the milliseconds per step of shape
+ * k to ms_per_step[k - 1] (-1 where a shape failed; as many entries as
+ * dugks_tile_shapes returns).  Synchronises.  Returns DUGKS_OK if at least
+ * one shape ran, else the first failure. */
+dugks_status dugks_autotune(const dugks_params *params, const double *phi0, const double *ux0, const double *uy0,
+                            const double *p0, int32_t trial_steps, void *cuda_stream, int32_t *best,
+                            double *ms_per_step);
 
 /* Creates a solver and builds the initial state psi~0 = psi_eq - dt/2 S with
  * d_t(phi u) = 0 (Eq. 23a with psi = psi_eq) from host fields phi0, ux0, uy0,

@@ -1,6 +1,7 @@
 // dugks_batch.cu -- batches of independent solvers advanced together.
 //
-// Members are grouped by kernel variant (precision x model x y-boundary).
+// Members are grouped by kernel variant (precision x model x y-boundary x
+// tile shape).
 // Each group owns a device array of per-problem descriptors (buffers,
 // constants, tensor maps, step counter) and a work list of (problem, tile)
 // items; one batched step is one launch per non-empty group plus a tiny
@@ -21,8 +22,11 @@ using dugks::fill_desc;
 
 namespace {
 
+constexpr int kMaxTiles = 4;   // compiled tile shapes per precision, at most
+
 struct Group {
     bool fp32 = false, coupled = false, wally = false;
+    int tile = 0;
     std::vector<dugks_ctx *> members;
     std::vector<unsigned char> h_desc;   // host image of the descriptor array
     std::vector<int2> h_work;
@@ -44,7 +48,7 @@ dugks_status from_cuda(cudaError_t e) {
 struct dugks_batch_ctx {
     cudaStream_t st = nullptr;
     std::vector<dugks_ctx *> members;
-    Group groups[8];   // index: fp32 * 4 + coupled * 2 + wally
+    Group groups[8 * kMaxTiles];   // index: (fp32 * 4 + coupled * 2 + wally) * kMaxTiles + tile
     bool dirty = true;
     cudaGraphExec_t exec = nullptr;
 
@@ -55,17 +59,20 @@ struct dugks_batch_ctx {
 
     // Rebuilds the host images (descriptors always, work lists when dirty) and uploads them.
     cudaError_t upload() {
-        for (int gi = 0; gi < 8; gi++) {
+        for (int gi = 0; gi < 8 * kMaxTiles; gi++) {
             Group &g = groups[gi];
             if (dirty) {
-                g.fp32 = gi & 4;
-                g.coupled = gi & 2;
-                g.wally = gi & 1;
+                const int v = gi / kMaxTiles;
+                g.fp32 = v & 4;
+                g.coupled = v & 2;
+                g.wally = v & 1;
+                g.tile = gi % kMaxTiles;
                 g.members.clear();
                 for (dugks_ctx *c : members)
-                    if (c->fp32 == g.fp32 && c->coupled == g.coupled && c->wally == g.wally) g.members.push_back(c);
-                const int tx = g.fp32 ? dugks::step_tile<float>(0) : dugks::step_tile<double>(0);
-                const int ty = g.fp32 ? dugks::step_tile<float>(1) : dugks::step_tile<double>(1);
+                    if (c->fp32 == g.fp32 && c->coupled == g.coupled && c->wally == g.wally && c->tile == g.tile)
+                        g.members.push_back(c);
+                const int tx = g.fp32 ? dugks::tile_dim<float>(g.tile, 0) : dugks::tile_dim<double>(g.tile, 0);
+                const int ty = g.fp32 ? dugks::tile_dim<float>(g.tile, 1) : dugks::tile_dim<double>(g.tile, 1);
                 g.h_work.clear();
                 for (size_t i = 0; i < g.members.size(); i++) {
                     const dugks_ctx *c = g.members[i];
@@ -77,7 +84,7 @@ struct dugks_batch_ctx {
             if (g.members.empty()) continue;
             const size_t ds = desc_size(g.fp32);
             g.h_desc.assign(ds * g.members.size(), 0);
-            const int tx = g.fp32 ? dugks::step_tile<float>(0) : dugks::step_tile<double>(0);
+            const int tx = g.fp32 ? dugks::tile_dim<float>(g.tile, 0) : dugks::tile_dim<double>(g.tile, 0);
             for (size_t i = 0; i < g.members.size(); i++) {
                 const dugks_ctx *c = g.members[i];
                 if (g.fp32)
@@ -114,10 +121,10 @@ struct dugks_batch_ctx {
     cudaError_t enqueue_step() {
         for (Group &g : groups) {
             if (g.members.empty()) continue;
-            cudaError_t e = g.fp32 ? dugks::launch_batch_step<float>(static_cast<InstDesc<float> *>(g.d_desc), g.d_work,
-                                                                     g.nwork, (int)g.members.size(), g.coupled,
-                                                                     g.wally, st)
-                                   : dugks::launch_batch_step<double>(static_cast<InstDesc<double> *>(g.d_desc),
+            cudaError_t e = g.fp32 ? dugks::launch_batch_step<float>(g.tile, static_cast<InstDesc<float> *>(g.d_desc),
+                                                                     g.d_work, g.nwork, (int)g.members.size(),
+                                                                     g.coupled, g.wally, st)
+                                   : dugks::launch_batch_step<double>(g.tile, static_cast<InstDesc<double> *>(g.d_desc),
                                                                       g.d_work, g.nwork, (int)g.members.size(),
                                                                       g.coupled, g.wally, st);
             if (e != cudaSuccess) return e;
@@ -128,8 +135,8 @@ struct dugks_batch_ctx {
     cudaError_t capture() {
         for (Group &g : groups) {
             if (g.members.empty()) continue;
-            cudaError_t e = g.fp32 ? dugks::batch_prepare<float>(g.coupled, g.wally)
-                                   : dugks::batch_prepare<double>(g.coupled, g.wally);
+            cudaError_t e = g.fp32 ? dugks::batch_prepare<float>(g.tile, g.coupled, g.wally)
+                                   : dugks::batch_prepare<double>(g.tile, g.coupled, g.wally);
             if (e != cudaSuccess) return e;
         }
         cudaGraph_t graph = nullptr;

@@ -42,9 +42,11 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 bool valid(const dugks_params *p) {
     if (!p) return false;
-    if (p->nx < 3 || p->ny < 3 || p->lattice != 9 || p->reserved != 0) return false;
+    if (p->nx < 3 || p->ny < 3 || p->lattice != 9) return false;
     if (p->model != DUGKS_COUPLED && p->model != DUGKS_AC_PRESCRIBED_U) return false;
     if (p->precision != DUGKS_FP64 && p->precision != DUGKS_FP32_SHIFTED) return false;
+    const int ntiles = p->precision == DUGKS_FP32_SHIFTED ? dugks::tile_count<float>() : dugks::tile_count<double>();
+    if (p->tile_shape < 0 || p->tile_shape > ntiles) return false;
     if (p->bc_x != DUGKS_BC_PERIODIC && p->bc_x != DUGKS_BC_WALL) return false;
     if (p->bc_y != DUGKS_BC_PERIODIC && p->bc_y != DUGKS_BC_WALL) return false;
     if (p->visc_interp != DUGKS_VISC_RECIPROCAL && p->visc_interp != DUGKS_VISC_LINEAR) return false;
@@ -230,6 +232,7 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
     c->fp32 = params->precision == DUGKS_FP32_SHIFTED;
     c->coupled = params->model == DUGKS_COUPLED;
     c->wally = params->bc_y == DUGKS_BC_WALL;
+    c->tile = params->tile_shape > 0 ? params->tile_shape - 1 : 0;
     c->st = static_cast<cudaStream_t>(cuda_stream);
     c->cur = 0;
     c->steps = 0;
@@ -252,8 +255,8 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
     }
 
     {
-        const int tx = c->fp32 ? dugks::step_tile<float>(0) : dugks::step_tile<double>(0);
-        const int ty = c->fp32 ? dugks::step_tile<float>(1) : dugks::step_tile<double>(1);
+        const int tx = c->fp32 ? dugks::tile_dim<float>(c->tile, 0) : dugks::tile_dim<double>(c->tile, 0);
+        const int ty = c->fp32 ? dugks::tile_dim<float>(c->tile, 1) : dugks::tile_dim<double>(c->tile, 1);
         c->tma_ok = true;
         for (int b = 0; b < 2; b++) {
             c->tma_ok = c->tma_ok && make_box_map(&c->tm_state[b], c->state(b), !c->fp32, params->nx, params->ny,
@@ -298,11 +301,11 @@ dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
     for (int64_t n = 0; n < nsteps; n++) {
         cudaError_t e;
         if (c->fp32)
-            e = dugks::launch_step<float>(c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<float>(), c->phf,
-                                          c->coupled, c->wally, c->st);
+            e = dugks::launch_step<float>(c->tile, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<float>(),
+                                          c->phf, c->coupled, c->wally, c->st);
         else
-            e = dugks::launch_step<double>(c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<double>(), c->phd,
-                                           c->coupled, c->wally, c->st);
+            e = dugks::launch_step<double>(c->tile, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<double>(),
+                                           c->phd, c->coupled, c->wally, c->st);
         if (e != cudaSuccess) return from_cuda(e);
         c->cur ^= 1;
         c->steps++;
@@ -444,6 +447,64 @@ dugks_status dugks_destroy(dugks_handle c) {
     }
     delete c;
     return from_cuda(e);
+}
+
+int32_t dugks_tile_shapes(int32_t precision, int32_t *tx, int32_t *ty, int32_t cap) {
+    if (precision != DUGKS_FP64 && precision != DUGKS_FP32_SHIFTED) return -1;
+    const bool f32 = precision == DUGKS_FP32_SHIFTED;
+    const int n = f32 ? dugks::tile_count<float>() : dugks::tile_count<double>();
+    for (int k = 0; k < n && k < cap; k++) {
+        if (tx) tx[k] = f32 ? dugks::tile_dim<float>(k, 0) : dugks::tile_dim<double>(k, 0);
+        if (ty) ty[k] = f32 ? dugks::tile_dim<float>(k, 1) : dugks::tile_dim<double>(k, 1);
+    }
+    return n;
+}
+
+dugks_status dugks_autotune(const dugks_params *params, const double *phi0, const double *ux0, const double *uy0,
+                            const double *p0, int32_t trial_steps, void *cuda_stream, int32_t *best,
+                            double *ms_per_step) {
+    if (!best || !valid(params) || !phi0 || trial_steps < 1) return DUGKS_ERR_ARG;
+    *best = 0;
+    const int32_t n = dugks_tile_shapes(params->precision, nullptr, nullptr, 0);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return DUGKS_ERR_CUDA;
+    }
+    dugks_status worst = DUGKS_OK;
+    float best_ms = 0.0f;
+    for (int32_t k = 0; k < n; k++) {
+        if (ms_per_step) ms_per_step[k] = -1.0;
+        dugks_params q = *params;
+        q.tile_shape = k + 1;
+        dugks_handle h = nullptr;
+        dugks_status r = dugks_create(&q, phi0, ux0, uy0, p0, nullptr, 0, cuda_stream, &h);
+        float ms = 0.0f;
+        if (r == DUGKS_OK) r = dugks_step(h, 2);   // warm-up: shared-memory attributes, caches
+        if (r == DUGKS_OK && cudaEventRecord(e0, st) != cudaSuccess) r = DUGKS_ERR_CUDA;
+        if (r == DUGKS_OK) r = dugks_step(h, trial_steps);
+        if (r == DUGKS_OK && cudaEventRecord(e1, st) != cudaSuccess) r = DUGKS_ERR_CUDA;
+        if (r == DUGKS_OK) r = dugks_sync(h);
+        if (r == DUGKS_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = DUGKS_ERR_CUDA;
+        if (h) {
+            const dugks_status rd = dugks_destroy(h);
+            if (r == DUGKS_OK) r = rd;
+        }
+        if (r != DUGKS_OK) {
+            if (worst == DUGKS_OK) worst = r;
+            continue;
+        }
+        ms /= (float)trial_steps;
+        if (ms_per_step) ms_per_step[k] = ms;
+        if (*best == 0 || ms < best_ms) {
+            *best = k + 1;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return *best > 0 ? DUGKS_OK : worst;
 }
 
 const char *dugks_status_string(dugks_status s) {

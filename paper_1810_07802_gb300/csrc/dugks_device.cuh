@@ -396,7 +396,7 @@ struct TileShape {
     static constexpr int AL = 128 / int(sizeof(Real));                         // 128-byte alignment
     static constexpr size_t up(size_t v) { return (v + AL - 1) / AL * AL; }
     static constexpr size_t off_box = 0;
-    static constexpr size_t off_hbox = off_box + size_t(NQ) * BXY;
+    static constexpr size_t off_hbox = up(off_box + size_t(NQ) * BXY);   // history planes (TMA-aligned)
     static constexpr size_t off_phi = up(off_hbox + size_t(2) * BXY);
     static constexpr size_t off_rec = up(off_phi + N2);
     static constexpr size_t off_aux = up(off_rec + size_t(RS) * N1);
@@ -408,7 +408,7 @@ struct TileShape {
     static constexpr size_t off_fx = off_box;
     static constexpr size_t off_fy = off_fx + (size_t(FS) * NFX + 3) / 4 * 4;
     static_assert(off_fy + size_t(FS) * NFY <= off_phi, "face fluxes must fit in the input box");
-    static_assert((size_t(NQ) * BXY * sizeof(Real)) % 128 == 0, "TMA destinations must be 128-byte aligned");
+    static_assert(off_hbox % AL == 0, "TMA destinations must be 128-byte aligned");
     static_assert((BX * sizeof(Real)) % 16 == 0, "TMA box rows must be multiples of 16 bytes");
     // CTAs per SM that the shared memory allows (228 KiB per SM, 1 KiB reserved per CTA);
     // passed to __launch_bounds__ so registers do not lower the occupancy further
@@ -689,8 +689,8 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
         s.Dx = Real(0);
         s.Dy = Real(0);
     } else {
-        s.Dx = (phux - box[S::NQ * BXY + e]) * ph.inv_dt;
-        s.Dy = (phuy - box[(S::NQ + 1) * BXY + e]) * ph.inv_dt;
+        s.Dx = (phux - box[S::off_hbox + e]) * ph.inv_dt;
+        s.Dy = (phuy - box[S::off_hbox + BXY + e]) * ph.inv_dt;
     }
     st4(aux + c1 * AS, s.dpx, s.dpy, s.lap, s.Dx);
     if (S::F64) aux[c1 * AS + 4] = s.Dy; else sdy[c1] = s.Dy;
@@ -781,7 +781,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
             mbar_init(bar, 1);
             mbar_expect_tx(bar, (uint32_t)((S::NQ + 2) * BXY * sizeof(Real)));
             tma_load_3d(box, tm_state_p, x0 - 4, y0 - 2, 0, bar);
-            tma_load_3d(box + S::NQ * BXY, tm_hist_p, x0 - 4, y0 - 2, 0, bar);
+            tma_load_3d(box + S::off_hbox, tm_hist_p, x0 - 4, y0 - 2, 0, bar);
             mode = 1;
             if (!mbar_wait(bar, 0, kPollLimit)) {
                 atomicOr(a.status, STATUS_TIMEOUT);
@@ -802,7 +802,8 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
             const int gx = wrap(x0 - 4 + bx, nx);
             const int gy = map_row<WALLY>(y0 - 2 + by, ny, true);
             const long long g = (long long)gy * pitch + gx;
-            box[e] = z < S::NQ ? a.src[z * plane + g] : a.hsrc[(z - S::NQ) * plane + g];
+            constexpr int HG = int(S::off_hbox) - S::NQ * BXY;   // alignment gap before the history planes
+            box[(HG != 0 && z >= S::NQ) ? e + HG : e] = z < S::NQ ? a.src[z * plane + g] : a.hsrc[(z - S::NQ) * plane + g];
         }
         __syncthreads();
     }

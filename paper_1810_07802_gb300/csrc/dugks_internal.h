@@ -18,12 +18,12 @@ template <typename Real> struct FieldArgs;
 template <typename Real> struct InstDesc;
 
 template <typename Real>
-cudaError_t launch_step(const CUtensorMap &tm_state, const CUtensorMap &tm_hist, const StepArgs<Real> &a,
+cudaError_t launch_step(int tile, const CUtensorMap &tm_state, const CUtensorMap &tm_hist, const StepArgs<Real> &a,
                         const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st);
 template <typename Real>
-size_t step_smem_bytes(bool coupled);
+int tile_count();
 template <typename Real>
-int step_tile(int axis);
+int tile_dim(int tile, int axis);   // 0 for a shape that is not compiled
 template <typename Real>
 cudaError_t launch_init(const double *in, Real *state, Real *hist, int nx, int ny, int pitch, long long plane,
                         const Phys<double> &ph, bool coupled, bool wally, cudaStream_t st);
@@ -34,10 +34,10 @@ template <typename Real>
 cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, double p_ref, double *dist,
                           double *hist_out, cudaStream_t st);
 template <typename Real>
-cudaError_t batch_prepare(bool coupled, bool wally);
+cudaError_t batch_prepare(int tile, bool coupled, bool wally);
 template <typename Real>
-cudaError_t launch_batch_step(InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled, bool wally,
-                              cudaStream_t st);
+cudaError_t launch_batch_step(int tile, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled,
+                              bool wally, cudaStream_t st);
 cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
                           int have_snap, double *partial, double *out, cudaStream_t st);
 
@@ -57,6 +57,7 @@ struct dugks_ctx {
     dugks_params P;
     dugks::Layout L;
     bool fp32, coupled, wally;
+    int tile;   // index of the compiled tile shape the step kernels use
     cudaStream_t st;
     unsigned char *ws;
     bool owns;
@@ -81,7 +82,7 @@ struct dugks_ctx {
     // Arguments of the next step (psi~^n in buffer cur).
     template <typename Real>
     dugks::StepArgs<Real> step_args() const {
-        const int tx = dugks::step_tile<Real>(0), ty = dugks::step_tile<Real>(1);
+        const int tx = dugks::tile_dim<Real>(tile, 0), ty = dugks::tile_dim<Real>(tile, 1);
         dugks::StepArgs<Real> a;
         a.src = static_cast<const Real *>(state(cur));
         a.dst = static_cast<Real *>(state(cur ^ 1));

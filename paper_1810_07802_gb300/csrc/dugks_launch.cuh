@@ -7,30 +7,47 @@
 #include "dugks_aux.cuh"
 #include "dugks_internal.h"
 
+#include <type_traits>
+
 namespace dugks {
 
-// Tile shapes (build-time; measured on GB300, see profiles/): FP64 favours
-// square tiles (least halo recompute for an ALU-bound step), FP32 wide tiles
-// (full 128-byte rows per warp).
-#ifndef DUGKS_TILE_F64_X
-#define DUGKS_TILE_F64_X 16
-#endif
-#ifndef DUGKS_TILE_F64_Y
-#define DUGKS_TILE_F64_Y 8
-#endif
-#ifndef DUGKS_TILE_F32_X
-#define DUGKS_TILE_F32_X 32
-#endif
-#ifndef DUGKS_TILE_F32_Y
-#define DUGKS_TILE_F32_Y 8
-#endif
-template <typename Real> struct Tile;
-template <> struct Tile<double> { static constexpr int TX = DUGKS_TILE_F64_X, TY = DUGKS_TILE_F64_Y; };
-template <> struct Tile<float> { static constexpr int TX = DUGKS_TILE_F32_X, TY = DUGKS_TILE_F32_Y; };
+// Tile shapes compiled into the library, per precision.  Shape 0 is the
+// default, chosen by sweeps on GB300 for large boxes (FP32 32 x 8: full
+// 128-byte rows per warp; FP64 16 x 8: least halo recompute for an ALU-bound
+// step); the narrower ones suit narrow domains (e.g. Nx = 4 channels) and are
+// candidates for the autotuner.
+template <typename Real> struct TileSet;
+template <> struct TileSet<float> {
+    static constexpr int N = 4;
+    static constexpr int TX[N] = {32, 16, 8, 4}, TY[N] = {8, 16, 32, 64};
+};
+template <> struct TileSet<double> {
+    static constexpr int N = 3;
+    static constexpr int TX[N] = {16, 8, 4}, TY[N] = {8, 16, 32};
+};
 
-template <typename Real, bool COUPLED, bool WALLY>
+// Calls f(std::integral_constant<int, V>) for the compiled shape V == v.
+template <typename Real, int V = 0, typename F>
+cudaError_t with_tile(int v, F &&f) {
+    if constexpr (V < TileSet<Real>::N) {
+        if (v == V) return f(std::integral_constant<int, V>{});
+        return with_tile<Real, V + 1>(v, f);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+// Calls f(bool_constant<COUPLED>, bool_constant<WALLY>).
+template <typename F>
+cudaError_t with_variant(bool coupled, bool wally, F &&f) {
+    using T = std::true_type;
+    using U = std::false_type;
+    if (coupled) return wally ? f(T{}, T{}) : f(T{}, U{});
+    return wally ? f(U{}, T{}) : f(U{}, U{});
+}
+
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
 static cudaError_t step_attr_t() {
-    constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
     using S = TileShape<Real, TX, TY, COUPLED>;
     static const cudaError_t attr = cudaFuncSetAttribute(step_kernel<Real, TX, TY, COUPLED, WALLY>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -41,67 +58,66 @@ static cudaError_t step_attr_t() {
     return attr != cudaSuccess ? attr : attr_solo;
 }
 
-// Must run outside stream capture (sets the kernel's shared-memory limit).
+// Must run outside stream capture (sets the kernels' shared-memory limit).
 template <typename Real>
-cudaError_t step_prepare(bool coupled, bool wally) {
-    if (coupled) return wally ? step_attr_t<Real, true, true>() : step_attr_t<Real, true, false>();
-    return wally ? step_attr_t<Real, false, true>() : step_attr_t<Real, false, false>();
-}
-
-template <typename Real, bool COUPLED, bool WALLY>
-static void batch_launch_t(const InstDesc<Real> *descs, const int2 *work, int nitems, cudaStream_t st) {
-    constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
-    using S = TileShape<Real, TX, TY, COUPLED>;
-    step_kernel<Real, TX, TY, COUPLED, WALLY><<<nitems, S::NT, S::smem_bytes, st>>>(descs, work);
+cudaError_t step_prepare(int tile, bool coupled, bool wally) {
+    return with_tile<Real>(tile, [&](auto v) {
+        constexpr int TX = TileSet<Real>::TX[decltype(v)::value], TY = TileSet<Real>::TY[decltype(v)::value];
+        return with_variant(coupled, wally, [&](auto c, auto w) {
+            return step_attr_t<Real, TX, TY, decltype(c)::value, decltype(w)::value>();
+        });
+    });
 }
 
 // One step of one problem: maps, arguments and constants by value.
 template <typename Real>
-cudaError_t launch_step(const CUtensorMap &tm_state, const CUtensorMap &tm_hist, const StepArgs<Real> &a,
+cudaError_t launch_step(int tile, const CUtensorMap &tm_state, const CUtensorMap &tm_hist, const StepArgs<Real> &a,
                         const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st) {
-    cudaError_t e = step_prepare<Real>(coupled, wally);
+    cudaError_t e = step_prepare<Real>(tile, coupled, wally);
     if (e != cudaSuccess) return e;
-    constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
-    const int tiles_x = (a.nx + TX - 1) / TX;
-    const int ntiles = tiles_x * ((a.ny + TY - 1) / TY);
-    if (coupled) {
-        using S = TileShape<Real, TX, TY, true>;
-        if (wally) solo_step_kernel<Real, TX, TY, true, true><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph, tiles_x);
-        else solo_step_kernel<Real, TX, TY, true, false><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph, tiles_x);
-    } else {
-        using S = TileShape<Real, TX, TY, false>;
-        if (wally) solo_step_kernel<Real, TX, TY, false, true><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph, tiles_x);
-        else solo_step_kernel<Real, TX, TY, false, false><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph, tiles_x);
-    }
-    return cudaGetLastError();
+    return with_tile<Real>(tile, [&](auto v) {
+        constexpr int TX = TileSet<Real>::TX[decltype(v)::value], TY = TileSet<Real>::TY[decltype(v)::value];
+        const int tiles_x = (a.nx + TX - 1) / TX;
+        const int ntiles = tiles_x * ((a.ny + TY - 1) / TY);
+        return with_variant(coupled, wally, [&](auto c, auto w) {
+            constexpr bool C = decltype(c)::value, W = decltype(w)::value;
+            using S = TileShape<Real, TX, TY, C>;
+            solo_step_kernel<Real, TX, TY, C, W><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph,
+                                                                                        tiles_x);
+            return cudaGetLastError();
+        });
+    });
 }
 
 template <typename Real>
-size_t step_smem_bytes(bool coupled) {
-    constexpr int TX = Tile<Real>::TX, TY = Tile<Real>::TY;
-    return coupled ? TileShape<Real, TX, TY, true>::smem_bytes : TileShape<Real, TX, TY, false>::smem_bytes;
-}
+int tile_count() { return TileSet<Real>::N; }
 
 template <typename Real>
-int step_tile(int axis) { return axis == 0 ? Tile<Real>::TX : Tile<Real>::TY; }
+int tile_dim(int tile, int axis) {
+    if (tile < 0 || tile >= TileSet<Real>::N) return 0;
+    return axis == 0 ? TileSet<Real>::TX[tile] : TileSet<Real>::TY[tile];
+}
 
 // ---- batched step ----
 template <typename Real>
-cudaError_t batch_prepare(bool coupled, bool wally) {
-    return step_prepare<Real>(coupled, wally);
+cudaError_t batch_prepare(int tile, bool coupled, bool wally) {
+    return step_prepare<Real>(tile, coupled, wally);
 }
 
 template <typename Real>
-cudaError_t launch_batch_step(InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled, bool wally,
-                              cudaStream_t st) {
+cudaError_t launch_batch_step(int tile, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled,
+                              bool wally, cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
-    if (coupled) {
-        if (wally) batch_launch_t<Real, true, true>(descs, work, nwork, st);
-        else batch_launch_t<Real, true, false>(descs, work, nwork, st);
-    } else {
-        if (wally) batch_launch_t<Real, false, true>(descs, work, nwork, st);
-        else batch_launch_t<Real, false, false>(descs, work, nwork, st);
-    }
+    cudaError_t e = with_tile<Real>(tile, [&](auto v) {
+        constexpr int TX = TileSet<Real>::TX[decltype(v)::value], TY = TileSet<Real>::TY[decltype(v)::value];
+        return with_variant(coupled, wally, [&](auto c, auto w) {
+            constexpr bool C = decltype(c)::value, W = decltype(w)::value;
+            using S = TileShape<Real, TX, TY, C>;
+            step_kernel<Real, TX, TY, C, W><<<nwork, S::NT, S::smem_bytes, st>>>(descs, work);
+            return cudaGetLastError();
+        });
+    });
+    if (e != cudaSuccess) return e;
     advance_kernel<Real><<<(ninst + 127) / 128, 128, 0, st>>>(descs, ninst);
     return cudaGetLastError();
 }
@@ -148,17 +164,18 @@ cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, doub
 }
 
 #define DUGKS_INSTANTIATE(Real)                                                                                     \
-    template cudaError_t launch_step<Real>(const CUtensorMap &, const CUtensorMap &, const StepArgs<Real> &,       \
+    template cudaError_t launch_step<Real>(int, const CUtensorMap &, const CUtensorMap &, const StepArgs<Real> &,  \
                                            const Phys<Real> &, bool, bool, cudaStream_t);                          \
-    template size_t step_smem_bytes<Real>(bool);                                                                    \
-    template int step_tile<Real>(int);                                                                              \
+    template int tile_count<Real>();                                                                                \
+    template int tile_dim<Real>(int, int);                                                                          \
     template cudaError_t launch_init<Real>(const double *, Real *, Real *, int, int, int, long long,                \
                                            const Phys<double> &, bool, bool, cudaStream_t);                         \
     template cudaError_t launch_macros<Real>(const FieldArgs<Real> &, double *, const Phys<double> &, bool, bool,  \
                                              double *, double *, double *, double *, cudaStream_t);                 \
     template cudaError_t launch_export<Real>(const FieldArgs<Real> &, int, double, double, double *, double *,     \
                                              cudaStream_t);                                                        \
-    template cudaError_t batch_prepare<Real>(bool, bool);                                                          \
-    template cudaError_t launch_batch_step<Real>(InstDesc<Real> *, const int2 *, int, int, bool, bool, cudaStream_t);
+    template cudaError_t batch_prepare<Real>(int, bool, bool);                                                     \
+    template cudaError_t launch_batch_step<Real>(int, InstDesc<Real> *, const int2 *, int, int, bool, bool,        \
+                                                 cudaStream_t);
 
 }  // namespace dugks

@@ -60,17 +60,46 @@ def summary(records):
             "mlups": updates / (t1 - t0) / 1e6}
 
 
+class AutotuneCache:
+    """Step-kernel tile shape per problem shape (precision, model, y-boundary,
+    nx, ny), measured once with dugks_autotune on the first problem of that
+    shape and reused for every later one."""
+
+    def __init__(self, trial_steps=10, tuner=None):
+        if tuner is None:
+            from . import solver as S
+
+            tuner = S.autotune
+        self.tuner, self.trial_steps = tuner, int(trial_steps)
+        self.shapes = {}
+        self.timings = {}
+
+    @staticmethod
+    def key(cfg):
+        return (cfg.get("precision", "fp64"), cfg.get("model", "coupled"), cfg.get("bc_y", "periodic"),
+                int(cfg["nx"]), int(cfg["ny"]))
+
+    def __call__(self, cfg, fields):
+        k = self.key(cfg)
+        if k not in self.shapes:
+            best, ms = self.tuner(cfg, trial_steps=self.trial_steps, **fields)
+            self.shapes[k], self.timings[k] = int(best), ms
+        return self.shapes[k]
+
+
 class BatchingServer:
     """Continuous batching with admission by device-memory footprint.
 
     hbm_budget: bytes of solver workspaces that may be resident at once.
     max_members: slots (resident problems) at most.
     chunk: steps enqueued between scheduling decisions at most.
+    tile_policy: None (the library's default tile shape) or a callable
+      (cfg, fields) -> tile_shape, e.g. an AutotuneCache.
     """
 
     def __init__(self, hbm_budget, max_members=128, chunk=50, stream=None, solver_factory=None,
                  batch_factory=None, footprint=None, clock=time.perf_counter, sleep=time.sleep,
-                 keep_results=True):
+                 keep_results=True, tile_policy=None):
         if solver_factory is None:
             import torch
 
@@ -89,10 +118,13 @@ class BatchingServer:
         self.make_solver, self.make_batch, self.footprint = solver_factory, batch_factory, footprint
         self.clock, self.sleep = clock, sleep
         self.keep_results = keep_results
+        self.tile_policy = tile_policy
 
     def run(self, requests):
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in reqs:
+            if self.tile_policy is not None and "tile_shape" not in r.cfg:
+                r.cfg = dict(r.cfg, tile_shape=int(self.tile_policy(r.cfg, r.fields)))
             if self.footprint(r.cfg) > self.hbm_budget:
                 raise ValueError("request %d needs more device memory than the whole budget" % r.rid)
         pending = collections.deque(reqs)

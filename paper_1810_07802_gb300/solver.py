@@ -21,7 +21,7 @@ class DugksParams(ctypes.Structure):
         ("model", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
         ("visc_interp", ctypes.c_int32), ("gravity_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tile_shape", ctypes.c_int32),
         ("cfl", ctypes.c_double), ("mobility", ctypes.c_double), ("width", ctypes.c_double),
         ("rho_h", ctypes.c_double), ("rho_l", ctypes.c_double),
         ("mu_h", ctypes.c_double), ("mu_l", ctypes.c_double), ("sigma", ctypes.c_double),
@@ -61,6 +61,10 @@ SIGNATURES = {
     "dugks_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "dugks_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "dugks_tile_shapes": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "dugks_autotune": (ctypes.c_int, [ctypes.POINTER(DugksParams), _dp, _dp, _dp, _dp, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), _dp]),
 }
 
 STATIC_REDUCE_MAX_CELLS = 16777216
@@ -122,7 +126,7 @@ def make_params(cfg):
     p.bc_y = _ENUM["bc"][cfg.get("bc_y", "periodic")]
     p.visc_interp = _ENUM["visc"][cfg.get("visc", "reciprocal")]
     p.gravity_mode = int(cfg.get("gravity_mode", 0))
-    p.reserved = 0
+    p.tile_shape = int(cfg.get("tile_shape", 0))
     for k in ("cfl", "mobility", "width", "rho_h", "rho_l", "mu_h", "mu_l", "sigma", "gx", "gy",
               "rho_ref", "phi_ref", "p_ref", "u0x", "u0y", "vel_u0", "vel_length"):
         setattr(p, k, float(cfg.get(k, 0.0)))
@@ -133,6 +137,35 @@ def make_params(cfg):
         p.phi_ref = float(cfg.get("phi_ref_fp64", 0.0))
         p.p_ref = float(cfg.get("p_ref_fp64", 0.0))
     return p
+
+
+def tile_shapes(precision="fp32"):
+    """Compiled step-kernel tile shapes [(tx, ty), ...]; cfg["tile_shape"] = k
+    selects entry k - 1 (0: the library default, entry 0)."""
+    prec = _ENUM["precision"][precision]
+    n = int(lib().dugks_tile_shapes(prec, None, None, 0))
+    tx, ty = (ctypes.c_int32 * n)(), (ctypes.c_int32 * n)()
+    lib().dugks_tile_shapes(prec, tx, ty, n)
+    return list(zip(tx[:], ty[:]))
+
+
+def autotune(cfg, phi0, ux0=None, uy0=None, p0=None, trial_steps=20, stream=None):
+    """Times every compiled tile shape on this problem (one at a time, in
+    library-allocated workspaces) and returns (best tile_shape value,
+    [ms per step of each shape, -1 where one failed])."""
+    import torch
+
+    params = make_params(cfg)
+    n = len(tile_shapes(cfg.get("precision", "fp64")))
+    shp = (params.ny, params.nx)
+    arrs = [_host(phi0, shp), _host(ux0, shp), _host(uy0, shp), _host(p0, shp)]
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    best = ctypes.c_int32(0)
+    ms = np.zeros(n)
+    code = lib().dugks_autotune(ctypes.byref(params), *[_ptr(a) for a in arrs], int(trial_steps),
+                                ctypes.c_void_p(stream.cuda_stream), ctypes.byref(best), _ptr(ms))
+    _check(code, "dugks_autotune")
+    return int(best.value), [float(v) for v in ms]
 
 
 def workspace_bytes(cfg):

@@ -72,3 +72,22 @@ def test_create_rejects_invalid_without_gpu(lib):
     assert lib.dugks_step(None, 1) == -1
     assert lib.dugks_step_count(None) == -1
     assert lib.dugks_status_string(-4) == b"non-finite value produced by a step"
+
+
+def test_tile_shapes_and_their_validation(lib):
+    """The compiled step-kernel tile shapes (no device work) and the range
+    check of params.tile_shape."""
+    f32 = solver.tile_shapes("fp32")
+    f64 = solver.tile_shapes("fp64")
+    assert f32[0] == (32, 8) and f64[0] == (16, 8)
+    for shapes in (f32, f64):
+        assert len(set(shapes)) == len(shapes) >= 2
+        for tx, ty in shapes:
+            assert tx % 4 == 0 and tx * ty >= 128
+    assert lib.dugks_tile_shapes(7, None, None, 0) == -1
+    cfg, _ = workloads.spinodal(N=64)
+    for prec, shapes in (("fp32", f32), ("fp64", f64)):
+        for k in range(len(shapes) + 1):
+            assert solver.workspace_bytes(dict(cfg, precision=prec, tile_shape=k)) > 0
+        assert solver.workspace_bytes(dict(cfg, precision=prec, tile_shape=len(shapes) + 1)) == 0
+        assert solver.workspace_bytes(dict(cfg, precision=prec, tile_shape=-1)) == 0

@@ -38,6 +38,11 @@ def problems():
     out.append((cfg, f))
     cfg, f = W.spinodal(N=96)
     out.append((dict(cfg, precision="fp32"), f))
+    # other compiled tile shapes form their own kernel groups
+    cfg, f = W.layered_poiseuille(ny=128, nx=4, mu_ratio=100.0)
+    out.append((dict(cfg, precision="fp32", phi_ref=0.5, tile_shape=4), f))
+    cfg, f = W.random_state(33, 40, seed=3)
+    out.append((dict(cfg, tile_shape=2), f))
     return out
 
 

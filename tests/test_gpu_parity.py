@@ -246,3 +246,40 @@ def test_zero_steps_is_identity(S):
         b = s.macros()
     for k in a:
         assert np.array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_every_tile_shape(S, precision):
+    """Each compiled tile shape of the step kernel against the oracle: periodic
+    and walled grids with interior (TMA-staged) and ragged edge tiles, and the
+    Allen-Cahn-only model."""
+    cases = [W.random_state(150, 70, seed=21), W.random_state(37, 29, seed=22, bc_y="wall"),
+             W.smoothed_deformation(L=48, U=0.04)]
+    for k, shape in enumerate(S.tile_shapes(precision), start=1):
+        for cfg, f in cases:
+            c = dict(cfg, precision=precision, tile_shape=k)
+            if precision == "fp32":
+                c.setdefault("phi_ref", 0.5)
+            with S.Solver(c, **f) as s:
+                s.step(6)
+                got = s.macros()
+                dist = s.distributions() if precision == "fp64" else None
+            o = Oracle(cfg, **f)
+            o.step(6)
+            ref = o.macros()
+            what = "%s tile %dx%d %dx%d" % (precision, shape[0], shape[1], cfg["nx"], cfg["ny"])
+            if precision == "fp64":
+                assert_parity(got, ref, dist, o.state(), what=what)
+            else:
+                assert np.abs(got["phi"] - ref["phi"]).max() <= 2e-5, what
+                assert np.abs(got["ux"] - ref["ux"]).max() <= 1e-7, what
+                assert np.abs(got["p"] - ref["p"]).max() <= 1e-5, what
+
+
+def test_autotune_picks_a_measured_shape(S):
+    cfg, f = W.layered_poiseuille(ny=256, nx=4, mu_ratio=100.0)
+    cfg = dict(cfg, precision="fp32", phi_ref=0.5)
+    best, ms = S.autotune(cfg, **f, trial_steps=5)
+    assert len(ms) == len(S.tile_shapes("fp32"))
+    assert all(m > 0 for m in ms)
+    assert 1 <= best <= len(ms) and ms[best - 1] == min(ms)

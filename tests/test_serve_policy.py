@@ -133,3 +133,31 @@ def test_batching_beats_sequential_on_a_burst():
     seq = SequentialServer(solver_factory=lambda r: SeqSolver(r, log), clock=clock, sleep=clock.sleep).run(reqs)
     assert summary(recs)["solves_per_s"] > summary(seq)["solves_per_s"]
     assert all(r.result["steps"] == q.steps for r, q in zip(seq, reqs))
+
+
+def test_autotune_cache_tunes_each_shape_once_and_server_applies_it():
+    from paper_1810_07802_gb300.serve import AutotuneCache
+
+    calls = []
+
+    def tuner(cfg, trial_steps, **fields):
+        calls.append(AutotuneCache.key(cfg))
+        return (2 if cfg["nx"] < 32 else 1), [1.0, 0.5]
+
+    cache = AutotuneCache(trial_steps=3, tuner=tuner)
+    clock, log, tracker = Clock(), [], {"max_members": 0}
+    seen = []
+
+    def make_solver(r):
+        seen.append((r.rid, r.cfg.get("tile_shape")))
+        return FakeSolver(r, log)
+
+    srv = BatchingServer(1 << 40, max_members=8, chunk=5, solver_factory=make_solver,
+                         batch_factory=lambda: FakeBatch(clock, tracker), footprint=footprint,
+                         clock=clock, sleep=clock.sleep, tile_policy=cache)
+    reqs = make_requests(20)
+    recs = srv.run(reqs)
+    assert len(recs) == 20
+    assert sorted(calls) == sorted(set(calls)) and len(calls) == 5      # 5 distinct shapes
+    for rid, shape in seen:
+        assert shape == (2 if reqs[rid].cfg["nx"] < 32 else 1)
