@@ -43,11 +43,20 @@
  *      adjacent cell's with the normal component removed (the mean of the
  *      cell and its mirror image), its lap phi is the adjacent cell's.
  *  R10 No clamping of phi, rho or mu.
- *  R11 Prescribed velocity fields of the A-C-only model are evaluated
+ *  R12 Prescribed velocity fields of the A-C-only model are evaluated
  *      analytically: at cell centres at t_n = n dt, at face centres at
  *      t_n + h (the time of the face distributions), with face coordinates
  *      taken in [0, nx) x [0, ny) on periodic axes.  The reversing shear
  *      (Eq. 42) changes sign for t >= L0/U0.
+ *  R14 Upwind reconstruction (recon = 1; Sec. II.B names the upwind scheme
+ *      as the alternative to the central one, and Sec. III.A the fix for
+ *      its high-Peclet error, without printing it): each of the two cells
+ *      sharing the face carries a linear profile of psi-bar-plus with
+ *      per-axis slopes from van Leer's limiter of its two one-sided
+ *      differences, sigma = 2 s1 s2 / (s1 + s2) if s1 s2 > 0 else 0; the
+ *      value at x_f - xi h is taken from the profile of the upwind cell
+ *      (the one xi . n points away from), and for xi . n = 0 it is the mean
+ *      of the two profiles.  Periodic boundaries only.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -203,7 +212,7 @@ void oracle_grad_lap(int nx, int ny, int wall_y, const double *phi,
         }
 }
 
-/* Prescribed velocity of the A-C-only model at (x, y), time t (R11). */
+/* Prescribed velocity of the A-C-only model at (x, y), time t (R12). */
 static void prescribed_velocity(const oracle_params *P, double x, double y, double t, double *ux, double *uy)
 {
     const double pi = 3.14159265358979323846;
@@ -421,6 +430,69 @@ static void recon_yface(const oracle_params *P, const double *B, int i, int jm, 
     }
 }
 
+/* van Leer's limiter of two one-sided differences: their harmonic mean, or 0
+ * at an extremum (R14). */
+static double van_leer(double s1, double s2)
+{
+    return s1 * s2 > 0.0 ? 2.0 * s1 * s2 / (s1 + s2) : 0.0;
+}
+
+/* R14 at the periodic x-face between columns i and i+1 of row j. */
+static void recon_xface_upwind(const oracle_params *P, const double *B, int i, int j, double *out)
+{
+    int nx = P->nx, ny = P->ny;
+    long N = (long)nx * ny;
+    double h = 0.5 * P->cfl;
+    int im = (i - 1 + nx) % nx, ip = (i + 1) % nx, ipp = (i + 2) % nx;
+    int jm = (j - 1 + ny) % ny, jp = (j + 1) % ny;
+    for (int q = 0; q < Q; q++) {
+        const double *b = B + q * N;
+        double L = b[(long)j * nx + i], R = b[(long)j * nx + ip];
+        double sxL = van_leer(L - b[(long)j * nx + im], R - L);
+        double sxR = van_leer(R - L, b[(long)j * nx + ipp] - R);
+        double syL = van_leer(L - b[(long)jm * nx + i], b[(long)jp * nx + i] - L);
+        double syR = van_leer(R - b[(long)jm * nx + ip], b[(long)jp * nx + ip] - R);
+        /* x_f - xi h relative to the centre of L is (1/2 - h ex, -h ey), of R (-1/2 - h ex, -h ey) */
+        double vL = L + sxL * (0.5 - h * EX[q]) + syL * (-h * EY[q]);
+        double vR = R + sxR * (-0.5 - h * EX[q]) + syR * (-h * EY[q]);
+        out[q] = EX[q] > 0 ? vL : (EX[q] < 0 ? vR : 0.5 * (vL + vR));
+    }
+}
+
+/* R14 at the periodic y-face between rows jm (below) and jc of column i. */
+static void recon_yface_upwind(const oracle_params *P, const double *B, int i, int jm, int jc, double *out)
+{
+    int nx = P->nx, ny = P->ny;
+    long N = (long)nx * ny;
+    double h = 0.5 * P->cfl;
+    int im = (i - 1 + nx) % nx, ip = (i + 1) % nx;
+    int jmm = (jm - 1 + ny) % ny, jcp = (jc + 1) % ny;
+    for (int q = 0; q < Q; q++) {
+        const double *b = B + q * N;
+        double D = b[(long)jm * nx + i], U = b[(long)jc * nx + i];
+        double syD = van_leer(D - b[(long)jmm * nx + i], U - D);
+        double syU = van_leer(U - D, b[(long)jcp * nx + i] - U);
+        double sxD = van_leer(D - b[(long)jm * nx + im], b[(long)jm * nx + ip] - D);
+        double sxU = van_leer(U - b[(long)jc * nx + im], b[(long)jc * nx + ip] - U);
+        /* x_f - xi h relative to the centre of D is (-h ex, 1/2 - h ey), of U (-h ex, -1/2 - h ey) */
+        double vD = D + sxD * (-h * EX[q]) + syD * (0.5 - h * EY[q]);
+        double vU = U + sxU * (-h * EX[q]) + syU * (-0.5 - h * EY[q]);
+        out[q] = EY[q] > 0 ? vD : (EY[q] < 0 ? vU : 0.5 * (vD + vU));
+    }
+}
+
+void oracle_face_bar(const oracle_params *P, const double *B, int i, int j, int xface, double *out)
+{
+    if (xface) {
+        if (P->recon == 1) recon_xface_upwind(P, B, i, j, out);
+        else recon_xface(P, B, i, j, out);
+    } else {
+        int jm = (j - 1 + P->ny) % P->ny;
+        if (P->recon == 1) recon_yface_upwind(P, B, i, jm, j, out);
+        else recon_yface(P, B, i, jm, j, out);
+    }
+}
+
 /* R9 at a wall face of column i: bottom (y = 0, top == 0) or top (y = ny). */
 static void recon_wall(const oracle_params *P, const double *B, int i, int top, double *out)
 {
@@ -489,8 +561,13 @@ static void one_step(oracle_ctx *c)
         for (int i = 0; i < nx; i++) {
             long kl = (long)j * nx + i, kr = (long)j * nx + (i + 1) % nx;
             double fb[Q], gb[Q] = {0}, fp[Q], gp[Q] = {0};
-            recon_xface(P, fbp, i, j, fb);
-            if (coupled) recon_xface(P, gbp, i, j, gb);
+            if (P->recon == 1) {
+                recon_xface_upwind(P, fbp, i, j, fb);
+                if (coupled) recon_xface_upwind(P, gbp, i, j, gb);
+            } else {
+                recon_xface(P, fbp, i, j, fb);
+                if (coupled) recon_xface(P, gbp, i, j, gb);
+            }
             face_distributions(c, fb, gb,
                                0.5 * (cs[kl].dphix + cs[kr].dphix), 0.5 * (cs[kl].dphiy + cs[kr].dphiy),
                                0.5 * (cs[kl].lap + cs[kr].lap),
@@ -515,8 +592,13 @@ static void one_step(oracle_ctx *c)
             } else {
                 int jm = (j - 1 + ny) % ny, jc = j % ny;
                 long kd = (long)jm * nx + i, ku = (long)jc * nx + i;
-                recon_yface(P, fbp, i, jm, jc, fb);
-                if (coupled) recon_yface(P, gbp, i, jm, jc, gb);
+                if (P->recon == 1) {
+                    recon_yface_upwind(P, fbp, i, jm, jc, fb);
+                    if (coupled) recon_yface_upwind(P, gbp, i, jm, jc, gb);
+                } else {
+                    recon_yface(P, fbp, i, jm, jc, fb);
+                    if (coupled) recon_yface(P, gbp, i, jm, jc, gb);
+                }
                 face_distributions(c, fb, gb,
                                    0.5 * (cs[kd].dphix + cs[ku].dphix), 0.5 * (cs[kd].dphiy + cs[ku].dphiy),
                                    0.5 * (cs[kd].lap + cs[ku].lap),
@@ -562,6 +644,7 @@ static int params_valid(const oracle_params *P)
     if (!(P->cfl > 0.0) || !(P->mobility > 0.0) || !(P->width > 0.0)) return 0;
     if (P->model != 0 && P->model != 1) return 0;
     if (P->velocity_field < 0 || P->velocity_field > 3) return 0;
+    if (P->recon < 0 || P->recon > 1 || (P->recon == 1 && P->wall_y)) return 0;
     if (P->model == 1 && P->velocity_field > 0 && (!(P->vel_u0 > 0.0) || !(P->vel_length > 0.0))) return 0;
     if (P->model == 0) {
         if (!(P->rho_h > 0.0) || !(P->rho_l > 0.0)) return 0;

@@ -45,6 +45,8 @@ typedef struct {
     int reserved;
     double vel_u0;       /* U0 of fields 1-3                                   */
     double vel_length;   /* L0 of fields 1-3                                   */
+    int recon;           /* 0 central (R2), 1 upwind with van Leer slopes (R14; periodic y only) */
+    int reserved2;
 } oracle_params;
 
 typedef struct oracle_ctx oracle_ctx;
@@ -85,6 +87,12 @@ void oracle_face_psi(double tau, double h, const double *bar, const double *eq,
  * Laplacian of phi, with periodic x and periodic-or-mirrored y. */
 void oracle_grad_lap(int nx, int ny, int wall_y, const double *phi,
                      double *dphix, double *dphiy, double *lap);
+
+/* Face value psi_bar(x_f, t + h) of every direction reconstructed from the
+ * grid B ([Q][ny][nx], psi-bar-plus) by the scheme params->recon selects, at
+ * the interior or periodic x-face i+1/2 of row j (xface != 0) or the y-face
+ * below row j of column i (xface == 0). */
+void oracle_face_bar(const oracle_params *params, const double *B, int i, int j, int xface, double *out);
 
 #ifdef __cplusplus
 }

@@ -28,12 +28,14 @@ class OracleParams(ctypes.Structure):
         ("u0x", ctypes.c_double), ("u0y", ctypes.c_double),
         ("velocity_field", ctypes.c_int), ("reserved", ctypes.c_int),
         ("vel_u0", ctypes.c_double), ("vel_length", ctypes.c_double),
+        ("recon", ctypes.c_int), ("reserved2", ctypes.c_int),
     ]
 
 
 _MODEL = {"coupled": 0, "ac": 1}
 _VISC = {"reciprocal": 0, "linear": 1}
 _FIELD = {"uniform": 0, "rotation": 1, "shear": 2, "deformation": 3}
+_RECON = {"central": 0, "upwind": 1}
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -62,6 +64,7 @@ def lib():
         L.oracle_prestep.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
         L.oracle_face_psi.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp]
         L.oracle_grad_lap.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+        L.oracle_face_bar.argtypes = [ctypes.POINTER(OracleParams), _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
         _lib = L
     return _lib
 
@@ -89,6 +92,7 @@ def make_params(cfg):
               "gx", "gy", "rho_ref", "u0x", "u0y", "vel_u0", "vel_length"):
         setattr(p, k, float(cfg.get(k, 0.0)))
     p.velocity_field = _FIELD[cfg.get("velocity_field", "uniform")]
+    p.recon = _RECON[cfg.get("recon", "central")]
     if cfg.get("bc_x", "periodic") != "periodic":
         raise ValueError("the oracle supports periodic x only")
     return p
@@ -207,3 +211,12 @@ def grad_lap(phi, wall_y=False):
     gx, gy, lp = np.zeros_like(phi), np.zeros_like(phi), np.zeros_like(phi)
     lib().oracle_grad_lap(nx, ny, 1 if wall_y else 0, _ptr(phi), _ptr(gx), _ptr(gy), _ptr(lp))
     return gx, gy, lp
+
+
+def face_bar(cfg, B, i, j, xface):
+    """psi_bar at one face from the grid B [Q][ny][nx] (central or upwind, per cfg["recon"])."""
+    p = make_params(cfg)
+    B = _f64(B, (Q, p.ny, p.nx))
+    out = np.zeros(Q)
+    lib().oracle_face_bar(ctypes.byref(p), _ptr(B), int(i), int(j), 1 if xface else 0, _ptr(out))
+    return out
