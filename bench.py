@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-upwind", action="store_true")
     return ap.parse_args()
 
 
@@ -187,13 +188,14 @@ def time_steps(solver, stream, steps):
     return start.elapsed_time(end) / 1e3
 
 
-def run_gpu_measure(precision, steps, warmup, world, rank):
+def run_gpu_measure(precision, steps, warmup, world, rank, recon="central"):
     import torch
     import torch.distributed as dist
 
     from paper_1810_07802_gb300 import solver as S
 
     cfg, f = workload(precision=precision)
+    cfg["recon"] = recon
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         s = S.Solver(cfg, stream=stream, **f)
@@ -344,6 +346,17 @@ def ours(args):
                          "ms_per_step": round(secs64 / k64 * 1e3, 4), "hbm_gbs": round(ach64, 1),
                          "hbm_frac": round(ach64 / peak_gbs, 4), "bound": "fp64 alu",
                          "clocks": clk64.summary()}
+    if not args.no_upwind:
+        # the upwind reconstruction (van Leer slopes) on the same workload, FP32-shifted
+        ku = max(3, min(args.steps, 200))
+        with ClockSampler(dev_index) as clku:
+            secsu, _ = run_gpu_measure("fp32", ku, 3, world, rank, recon="upwind")
+        achu = FP32_BYTES_PER_CELL * cells / (secsu / ku) / 1e9
+        extra["upwind_fp32"] = {"value": round(cells * ku / secsu / 1e6 * world, 1), "unit": "MLUPS", "steps": ku,
+                                "ms_per_step": round(secsu / ku * 1e3, 5), "hbm_gbs": round(achu, 1),
+                                "hbm_frac": round(achu / peak_gbs, 4),
+                                "kernel": "solo_step_kernel<float,32,8,coupled,periodic,upwind>",
+                                "clocks": clku.summary()}
 
     line = {"metric": "coupled DUGKS MLUPS (spinodal 2048^2, FP32-shifted)", "value": round(value, 1),
             "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -56,6 +56,13 @@ typedef enum { DUGKS_BC_PERIODIC = 0, DUGKS_BC_WALL = 1 } dugks_bc;
 typedef enum { DUGKS_FP64 = 0, DUGKS_FP32_SHIFTED = 1 } dugks_precision;
 typedef enum { DUGKS_COUPLED = 0, DUGKS_AC_PRESCRIBED_U = 1 } dugks_model;
 typedef enum { DUGKS_VISC_RECIPROCAL = 0, DUGKS_VISC_LINEAR = 1 } dugks_visc;
+/* Reconstruction of psi-bar-plus at x_f - xi h (Eq. 27).  Central: linear
+ * profile through the face (Sec. II.B's choice).  Upwind: each cell of the
+ * face carries a linear profile with van Leer-limited slopes, and a direction
+ * takes the profile of the cell it leaves (the mean of both when it runs
+ * along the face); the scheme Sec. II.B names as the alternative and Sec.
+ * III.A as the remedy for the error growth at high Peclet number. */
+typedef enum { DUGKS_RECON_CENTRAL = 0, DUGKS_RECON_UPWIND = 1 } dugks_recon;
 
 /*
  * Problem statement (Sec. II.A-B).  phi_H = 1 is the heavy phase, phi_L = 0
@@ -95,6 +102,11 @@ typedef struct {
     int32_t reserved2;     /* must be 0                                            */
     double vel_u0;         /* U0 > 0 of velocity fields 1-3                        */
     double vel_length;     /* L0 > 0 of velocity fields 1-3                        */
+    int32_t recon;         /* dugks_recon: reconstruction of psi-bar-plus at
+                              x_f - xi h (Eq. 27): central (default, Sec. II.B) or
+                              upwind with van Leer-limited slopes (periodic y and
+                              the default tile shape only)                         */
+    int32_t reserved3;     /* must be 0                                            */
 } dugks_params;
 
 typedef struct dugks_ctx *dugks_handle;

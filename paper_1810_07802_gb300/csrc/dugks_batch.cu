@@ -1,7 +1,7 @@
 // dugks_batch.cu -- batches of independent solvers advanced together.
 //
 // Members are grouped by kernel variant (precision x model x y-boundary x
-// tile shape).
+// tile shape x reconstruction).
 // Each group owns a device array of per-problem descriptors (buffers,
 // constants, tensor maps, step counter) and a work list of (problem, tile)
 // items; one batched step is one launch per non-empty group plus a tiny
@@ -25,7 +25,7 @@ namespace {
 constexpr int kMaxTiles = 4;   // compiled tile shapes per precision, at most
 
 struct Group {
-    bool fp32 = false, coupled = false, wally = false;
+    bool fp32 = false, coupled = false, wally = false, upw = false;
     int tile = 0;
     std::vector<dugks_ctx *> members;
     std::vector<unsigned char> h_desc;   // host image of the descriptor array
@@ -48,7 +48,8 @@ dugks_status from_cuda(cudaError_t e) {
 struct dugks_batch_ctx {
     cudaStream_t st = nullptr;
     std::vector<dugks_ctx *> members;
-    Group groups[8 * kMaxTiles];   // index: (fp32 * 4 + coupled * 2 + wally) * kMaxTiles + tile
+    static constexpr int kGroups = 16 * kMaxTiles;
+    Group groups[kGroups];   // index: (upw * 8 + fp32 * 4 + coupled * 2 + wally) * kMaxTiles + tile
     bool dirty = true;
     cudaGraphExec_t exec = nullptr;
 
@@ -59,17 +60,19 @@ struct dugks_batch_ctx {
 
     // Rebuilds the host images (descriptors always, work lists when dirty) and uploads them.
     cudaError_t upload() {
-        for (int gi = 0; gi < 8 * kMaxTiles; gi++) {
+        for (int gi = 0; gi < kGroups; gi++) {
             Group &g = groups[gi];
             if (dirty) {
                 const int v = gi / kMaxTiles;
+                g.upw = v & 8;
                 g.fp32 = v & 4;
                 g.coupled = v & 2;
                 g.wally = v & 1;
                 g.tile = gi % kMaxTiles;
                 g.members.clear();
                 for (dugks_ctx *c : members)
-                    if (c->fp32 == g.fp32 && c->coupled == g.coupled && c->wally == g.wally && c->tile == g.tile)
+                    if (c->fp32 == g.fp32 && c->coupled == g.coupled && c->wally == g.wally && c->tile == g.tile &&
+                        c->upw == g.upw)
                         g.members.push_back(c);
                 const int tx = g.fp32 ? dugks::tile_dim<float>(g.tile, 0) : dugks::tile_dim<double>(g.tile, 0);
                 const int ty = g.fp32 ? dugks::tile_dim<float>(g.tile, 1) : dugks::tile_dim<double>(g.tile, 1);
@@ -121,10 +124,10 @@ struct dugks_batch_ctx {
     cudaError_t enqueue_step() {
         for (Group &g : groups) {
             if (g.members.empty()) continue;
-            cudaError_t e = g.fp32 ? dugks::launch_batch_step<float>(g.tile, static_cast<InstDesc<float> *>(g.d_desc),
+            cudaError_t e = g.fp32 ? dugks::launch_batch_step<float>(g.tile, g.upw, static_cast<InstDesc<float> *>(g.d_desc),
                                                                      g.d_work, g.nwork, (int)g.members.size(),
                                                                      g.coupled, g.wally, st)
-                                   : dugks::launch_batch_step<double>(g.tile, static_cast<InstDesc<double> *>(g.d_desc),
+                                   : dugks::launch_batch_step<double>(g.tile, g.upw, static_cast<InstDesc<double> *>(g.d_desc),
                                                                       g.d_work, g.nwork, (int)g.members.size(),
                                                                       g.coupled, g.wally, st);
             if (e != cudaSuccess) return e;
@@ -135,8 +138,8 @@ struct dugks_batch_ctx {
     cudaError_t capture() {
         for (Group &g : groups) {
             if (g.members.empty()) continue;
-            cudaError_t e = g.fp32 ? dugks::batch_prepare<float>(g.tile, g.coupled, g.wally)
-                                   : dugks::batch_prepare<double>(g.tile, g.coupled, g.wally);
+            cudaError_t e = g.fp32 ? dugks::batch_prepare<float>(g.tile, g.coupled, g.wally, g.upw)
+                                   : dugks::batch_prepare<double>(g.tile, g.coupled, g.wally, g.upw);
             if (e != cudaSuccess) return e;
         }
         cudaGraph_t graph = nullptr;

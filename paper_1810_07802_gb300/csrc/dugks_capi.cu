@@ -47,6 +47,8 @@ bool valid(const dugks_params *p) {
     if (p->precision != DUGKS_FP64 && p->precision != DUGKS_FP32_SHIFTED) return false;
     const int ntiles = p->precision == DUGKS_FP32_SHIFTED ? dugks::tile_count<float>() : dugks::tile_count<double>();
     if (p->tile_shape < 0 || p->tile_shape > ntiles) return false;
+    if (p->recon != DUGKS_RECON_CENTRAL && p->recon != DUGKS_RECON_UPWIND) return false;
+    if (p->reserved3 != 0) return false;
     if (p->bc_x != DUGKS_BC_PERIODIC && p->bc_x != DUGKS_BC_WALL) return false;
     if (p->bc_y != DUGKS_BC_PERIODIC && p->bc_y != DUGKS_BC_WALL) return false;
     if (p->visc_interp != DUGKS_VISC_RECIPROCAL && p->visc_interp != DUGKS_VISC_LINEAR) return false;
@@ -221,6 +223,8 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
     *out = nullptr;
     if (!valid(params) || !phi0) return DUGKS_ERR_ARG;
     if (params->bc_x != DUGKS_BC_PERIODIC) return DUGKS_ERR_UNSUPPORTED;
+    if (params->recon == DUGKS_RECON_UPWIND && (params->bc_y != DUGKS_BC_PERIODIC || params->tile_shape > 1))
+        return DUGKS_ERR_UNSUPPORTED;
     const Layout L = layout(params);
     if (device_workspace && (reinterpret_cast<uintptr_t>(device_workspace) % kAlign)) return DUGKS_ERR_ARG;
     if (device_workspace && ws_bytes < L.total) return DUGKS_ERR_OOM;
@@ -233,6 +237,7 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
     c->coupled = params->model == DUGKS_COUPLED;
     c->wally = params->bc_y == DUGKS_BC_WALL;
     c->tile = params->tile_shape > 0 ? params->tile_shape - 1 : 0;
+    c->upw = params->recon == DUGKS_RECON_UPWIND;
     c->st = static_cast<cudaStream_t>(cuda_stream);
     c->cur = 0;
     c->steps = 0;
@@ -256,13 +261,14 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
 
     {
         const int tx = c->fp32 ? dugks::tile_dim<float>(c->tile, 0) : dugks::tile_dim<double>(c->tile, 0);
-        const int ty = c->fp32 ? dugks::tile_dim<float>(c->tile, 1) : dugks::tile_dim<double>(c->tile, 1);
+        const int box_rows = c->fp32 ? dugks::step_box_rows<float>(c->tile, c->upw)
+                                     : dugks::step_box_rows<double>(c->tile, c->upw);
         c->tma_ok = true;
         for (int b = 0; b < 2; b++) {
             c->tma_ok = c->tma_ok && make_box_map(&c->tm_state[b], c->state(b), !c->fp32, params->nx, params->ny,
-                                                  L.pitch, L.nq, tx + 8, ty + 4);
+                                                  L.pitch, L.nq, tx + 8, box_rows);
             c->tma_ok = c->tma_ok && make_box_map(&c->tm_hist[b], c->hist(b), !c->fp32, params->nx, params->ny,
-                                                  L.pitch, 2, tx + 8, ty + 4);
+                                                  L.pitch, 2, tx + 8, box_rows);
         }
     }
     cudaError_t e = cudaMemsetAsync(c->ws, 0, L.off_stage, c->st);  // state, history (incl. row padding)
@@ -301,10 +307,10 @@ dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
     for (int64_t n = 0; n < nsteps; n++) {
         cudaError_t e;
         if (c->fp32)
-            e = dugks::launch_step<float>(c->tile, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<float>(),
+            e = dugks::launch_step<float>(c->tile, c->upw, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<float>(),
                                           c->phf, c->coupled, c->wally, c->st);
         else
-            e = dugks::launch_step<double>(c->tile, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<double>(),
+            e = dugks::launch_step<double>(c->tile, c->upw, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<double>(),
                                            c->phd, c->coupled, c->wally, c->st);
         if (e != cudaSuccess) return from_cuda(e);
         c->cur ^= 1;

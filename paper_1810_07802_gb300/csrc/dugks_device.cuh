@@ -371,19 +371,23 @@ __device__ __forceinline__ void st2(double *p, double a, double b) { *reinterpre
 #define DUGKS_EXTRA_WARPS_F64 2
 #endif
 
-template <typename Real, int TX, int TY, bool COUPLED>
+// UPW: the upwind reconstruction (R14) reads psi-bar-plus two cells from a
+// face, so its records cover the tile + 2 cells (H = 2) instead of + 1.
+template <typename Real, int TX, int TY, bool COUPLED, bool UPW = false>
 struct TileShape {
     static constexpr bool F64 = sizeof(Real) == 8;
+    static constexpr int H = UPW ? 2 : 1;                                         // record halo
     static constexpr int NC = TX * TY;                                            // tile cells
     static constexpr int NT = NC + 32 * (F64 ? DUGKS_EXTRA_WARPS_F64 : DUGKS_EXTRA_WARPS_F32);  // threads
-    static constexpr int HX2 = TX + 4, HY2 = TY + 4;  // phi region (halo 2)
-    static constexpr int HX1 = TX + 2, HY1 = TY + 2;  // psi-bar-plus region (halo 1)
+    static constexpr int HX2 = TX + 2 * H + 2, HY2 = TY + 2 * H + 2;  // phi' region (halo H + 1)
+    static constexpr int HX1 = TX + 2 * H, HY1 = TY + 2 * H;          // psi-bar-plus records (halo H)
     static constexpr int N2 = HX2 * HY2, N1 = HX1 * HY1;
     static constexpr int NQ = COUPLED ? 18 : 9;
     // Input box: columns x0-4 .. x0+TX+3 (the left edge rounded down to a
-    // 16-byte boundary for TMA), rows y0-2 .. y0+TY+1, the NQ distribution
-    // planes followed by the 2 history planes.
-    static constexpr int BX = TX + 8, BY = TY + 4, BXY = BX * BY;
+    // 16-byte boundary for TMA; covers the phi' region for H <= 2), rows
+    // y0-H-1 .. y0+TY+H, the NQ distribution planes followed by the 2
+    // history planes.
+    static constexpr int BX = TX + 8, BY = TY + 2 * H + 2, BXY = BX * BY;
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
 #ifndef DUGKS_FACE_PAD
 #define DUGKS_FACE_PAD 1
@@ -507,6 +511,58 @@ __device__ __forceinline__ void recon_face(const Real *__restrict__ rec, int A, 
                 else T = (a[j] + b[j]) - (as[j] + bs[j]);
                 v = ct > 0 ? v - ht * T : v + ht * T;
             }
+            if (m == 0) fb[k] = v; else gb[k] = v;
+        }
+    }
+}
+
+// van Leer's limiter of two one-sided differences: their harmonic mean, or 0
+// at an extremum (R14).
+template <typename Real>
+__device__ __forceinline__ Real van_leer(Real s1, Real s2) {
+    return s1 * s2 > Real(0) ? Real(2) * s1 * s2 * rcp_r(s1 + s2) : Real(0);
+}
+
+// Upwind reconstruction (R14) at the face between cells A and B (record
+// indices; B = A + nstride along the face normal): each cell carries a linear
+// profile with van Leer slopes along the normal (cells A - nstride .. B +
+// nstride) and the tangent (A +- tstride, B +- tstride); a direction crossing
+// the face takes the upwind cell's profile at x_f - xi h, one along the face
+// the mean of both.  The rest direction of g is not needed and is skipped.
+template <typename Real, bool COUPLED, bool XFACE, int RS>
+__device__ __forceinline__ void recon_face_upwind(const Real *__restrict__ rec, int A, int B, int nstride,
+                                                  int tstride, Real h, Real fb[9], Real gb[9]) {
+#pragma unroll
+    for (int G = 0; G < Rec<COUPLED>::NG; G++) {
+        Real a[4], b[4], am[4], bp[4], an[4], as[4], bn[4], bs[4];
+        ld4(rec + A * RS + 4 * G, a);
+        ld4(rec + B * RS + 4 * G, b);
+        ld4(rec + (A - nstride) * RS + 4 * G, am);
+        ld4(rec + (B + nstride) * RS + 4 * G, bp);
+        if (group_tangential<COUPLED, XFACE>(G)) {
+            ld4(rec + (A + tstride) * RS + 4 * G, an);
+            ld4(rec + (A - tstride) * RS + 4 * G, as);
+            ld4(rec + (B + tstride) * RS + 4 * G, bn);
+            ld4(rec + (B - tstride) * RS + 4 * G, bs);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int s = 4 * G + j;
+            if (!Rec<COUPLED>::used(s)) continue;
+            const int k = Rec<COUPLED>::dir(s), m = Rec<COUPLED>::model(s);
+            if (m == 1 && k == 0) continue;
+            const int cn = XFACE ? cx(k) : cy(k), ct = XFACE ? cy(k) : cx(k);
+            // A's profile at x_f - xi h: normal offset 1/2 - h cn, tangential -h ct; B's: -1/2 - h cn
+            Real vA = Real(0), vB = Real(0);
+            if (cn >= 0) {
+                vA = a[j] + van_leer(a[j] - am[j], b[j] - a[j]) * (cn > 0 ? Real(0.5) - h : Real(0.5));
+                if (ct != 0) vA -= sgnmul(ct, h * van_leer(a[j] - as[j], an[j] - a[j]));
+            }
+            if (cn <= 0) {
+                vB = b[j] + van_leer(b[j] - a[j], bp[j] - b[j]) * (cn < 0 ? h - Real(0.5) : Real(-0.5));
+                if (ct != 0) vB -= sgnmul(ct, h * van_leer(b[j] - bs[j], bn[j] - b[j]));
+            }
+            const Real v = cn > 0 ? vA : (cn < 0 ? vB : Real(0.5) * (vA + vB));
             if (m == 0) fb[k] = v; else gb[k] = v;
         }
     }
@@ -646,15 +702,16 @@ __device__ __forceinline__ void phi_stencils(const Real *__restrict__ p, int c, 
 // halo-1 region (record index c1, box index e), from the staged box.  For a
 // tile cell (TILE) also psi~+ partials tp = 4/3 psi-bar-plus - 1/3 psi~
 // (Eq. 30) and the new (phi u) history.
-template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool TILE>
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW, bool TILE>
 __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Real> &ph, const Real *__restrict__ box,
                                           const Real *__restrict__ sphi, Real *__restrict__ rec, Real *__restrict__ aux,
                                           Real *__restrict__ sdy, int hx, int hy, int x0, int y0, Real tp[18]) {
-    using S = TileShape<Real, TX, TY, COUPLED>;
+    using S = TileShape<Real, TX, TY, COUPLED, UPW>;
     using R = Rec<COUPLED>;
     constexpr int RS = S::RS, AS = S::AS, BXY = S::BXY;
+    constexpr int H = S::H;
     const int c1 = hy * S::HX1 + hx;
-    const int yraw = y0 + hy - 1;
+    const int yraw = y0 + hy - H;
     if (WALLY && (yraw < 0 || yraw >= a.ny)) {
         // outside the walls: never read by a face; keep the smem defined
 #pragma unroll
@@ -663,7 +720,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
         if (S::F64) aux[c1 * AS + 4] = Real(0); else sdy[c1] = Real(0);
         return;
     }
-    const int e = (hy + 1) * S::BX + hx + 3;
+    const int e = (hy + 1) * S::BX + hx + 4 - H;
     Pt<Real> s;
     const int c2 = (hy + 1) * S::HX2 + (hx + 1);
     phi_stencils(sphi, c2, S::HX2, s.dpx, s.dpy, s.lap);
@@ -680,7 +737,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
         s.ux = ph.u0x;
         s.uy = ph.u0y;
     } else {
-        const int gx = a.small ? wrap(x0 + hx - 1, a.nx) : wrap1(x0 + hx - 1, a.nx);
+        const int gx = a.small ? wrap(x0 + hx - H, a.nx) : wrap1(x0 + hx - H, a.nx);
         const int gy = WALLY ? yraw : (a.small ? wrap(yraw, a.ny) : wrap1(yraw, a.ny));
         prescribed_velocity(ph, Real(gx) + Real(0.5), Real(gy) + Real(0.5), a.t_n, s.ux, s.uy);
     }
@@ -723,8 +780,8 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
 #pragma unroll
     for (int G = 0; G < R::NG; G++) st4(rec + c1 * RS + 4 * G, r[4 * G], r[4 * G + 1], r[4 * G + 2], r[4 * G + 3]);
 
-    if (TILE && x0 + hx - 1 < a.nx && yraw < a.ny) {
-        const long long g = (long long)yraw * a.pitch + (x0 + hx - 1);
+    if (TILE && x0 + hx - H < a.nx && yraw < a.ny) {
+        const long long g = (long long)yraw * a.pitch + (x0 + hx - H);
         a.hdst[g] = phux;
         a.hdst[a.plane + g] = phuy;
         const bool bad = !finite_r(s.phi) || !finite_r(s.ux) || !finite_r(s.uy);
@@ -751,10 +808,11 @@ constexpr long kPollLimit = 1l << 16;
 //      (face records reuse the box)
 //   4. the flux update (Eq. 24) of the tile to global
 // ---------------------------------------------------------------------------
-template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
                                           const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0) {
-    using S = TileShape<Real, TX, TY, COUPLED>;
+    static_assert(!(UPW && WALLY), "the upwind reconstruction is defined for periodic boundaries only");
+    using S = TileShape<Real, TX, TY, COUPLED, UPW>;
     constexpr int RS = S::RS, AS = S::AS, FS = S::FS, BX = S::BX, BXY = S::BXY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 128-byte aligned base for the TMA destinations, whatever the runtime gives
@@ -774,14 +832,15 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     const long long plane = a.plane;
 
     // 0. stage the input box [NQ + 2][BY][BX]
-    const bool interior = a.use_tma && x0 >= 4 && x0 + TX + 4 <= nx && y0 >= 2 && y0 + TY + 2 <= ny;
+    constexpr int H = S::H;
+    const bool interior = a.use_tma && x0 >= 4 && x0 + TX + 4 <= nx && y0 >= H + 1 && y0 + TY + H + 1 <= ny;
     if (tid == 0) {
         int mode = 0;  // 0: plain loads, 1: staged by TMA, 2: TMA timed out
         if (interior && !(*((volatile unsigned *)a.status) & STATUS_TIMEOUT)) {
             mbar_init(bar, 1);
             mbar_expect_tx(bar, (uint32_t)((S::NQ + 2) * BXY * sizeof(Real)));
-            tma_load_3d(box, tm_state_p, x0 - 4, y0 - 2, 0, bar);
-            tma_load_3d(box + S::off_hbox, tm_hist_p, x0 - 4, y0 - 2, 0, bar);
+            tma_load_3d(box, tm_state_p, x0 - 4, y0 - H - 1, 0, bar);
+            tma_load_3d(box + S::off_hbox, tm_hist_p, x0 - 4, y0 - H - 1, 0, bar);
             mode = 1;
             if (!mbar_wait(bar, 0, kPollLimit)) {
                 atomicOr(a.status, STATUS_TIMEOUT);
@@ -800,7 +859,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
         for (int e = tid; e < (S::NQ + 2) * BXY; e += S::NT) {
             const int z = e / BXY, r = e - z * BXY, by = r / BX, bx = r - by * BX;
             const int gx = wrap(x0 - 4 + bx, nx);
-            const int gy = map_row<WALLY>(y0 - 2 + by, ny, true);
+            const int gy = map_row<WALLY>(y0 - H - 1 + by, ny, true);
             const long long g = (long long)gy * pitch + gx;
             constexpr int HG = int(S::off_hbox) - S::NQ * BXY;   // alignment gap before the history planes
             box[(HG != 0 && z >= S::NQ) ? e + HG : e] = z < S::NQ ? a.src[z * plane + g] : a.hsrc[(z - S::NQ) * plane + g];
@@ -808,10 +867,10 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
         __syncthreads();
     }
 
-    // 1. phi' on the halo-2 region
+    // 1. phi' on the halo-(H+1) region
     for (int t = tid; t < S::N2; t += S::NT) {
         const int lx = t % S::HX2, ly = t / S::HX2;
-        const Real *p = box + ly * BX + lx + 2;
+        const Real *p = box + ly * BX + lx + 3 - H;
         Real s = p[0];
 #pragma unroll
         for (int k = 1; k < 9; k++) s += p[k * BXY];
@@ -823,16 +882,26 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     //    registers of threads 0..NC-1), items t >= NC the halo ring
     Real tp[18];
     if (tid < S::NC)
-        cell_item<Real, TX, TY, COUPLED, WALLY, true>(a, ph, box, sphi, rec, aux, sdy, tid % TX + 1, tid / TX + 1,
-                                                      x0, y0, tp);
+        cell_item<Real, TX, TY, COUPLED, WALLY, UPW, true>(a, ph, box, sphi, rec, aux, sdy, tid % TX + H,
+                                                           tid / TX + H, x0, y0, tp);
     for (int t = tid < S::NC ? tid + S::NT : tid; t < S::N1; t += S::NT) {
         const int r = t - S::NC;
         int hx, hy;
-        if (r < S::HX1) { hx = r; hy = 0; }
-        else if (r < 2 * S::HX1) { hx = r - S::HX1; hy = S::HY1 - 1; }
-        else if (r < 2 * S::HX1 + TY) { hx = 0; hy = r - 2 * S::HX1 + 1; }
-        else { hx = S::HX1 - 1; hy = r - 2 * S::HX1 - TY + 1; }
-        cell_item<Real, TX, TY, COUPLED, WALLY, false>(a, ph, box, sphi, rec, aux, sdy, hx, hy, x0, y0, nullptr);
+        if (H == 1) {   // ring: top row, bottom row, left column, right column
+            if (r < S::HX1) { hx = r; hy = 0; }
+            else if (r < 2 * S::HX1) { hx = r - S::HX1; hy = S::HY1 - 1; }
+            else if (r < 2 * S::HX1 + TY) { hx = 0; hy = r - 2 * S::HX1 + 1; }
+            else { hx = S::HX1 - 1; hy = r - 2 * S::HX1 - TY + 1; }
+        } else {        // H top rows, H bottom rows, then H cells on each side of every tile row
+            if (r < H * S::HX1) { hx = r % S::HX1; hy = r / S::HX1; }
+            else if (r < 2 * H * S::HX1) { hx = (r - H * S::HX1) % S::HX1; hy = S::HY1 - H + (r - H * S::HX1) / S::HX1; }
+            else {
+                const int r3 = r - 2 * H * S::HX1, k = r3 % (2 * H);
+                hy = H + r3 / (2 * H);
+                hx = k < H ? k : TX + k;
+            }
+        }
+        cell_item<Real, TX, TY, COUPLED, WALLY, UPW, false>(a, ph, box, sphi, rec, aux, sdy, hx, hy, x0, y0, nullptr);
     }
     __syncthreads();
 
@@ -847,10 +916,14 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
             const int fx = t % (TX + 1), fy = t / (TX + 1);
             const int gyr = y0 + fy;
             if (gyr >= ny || x0 + fx - 1 >= nx) continue;
-            const int L = (fy + 1) * S::HX1 + fx, Rr = L + 1;
-            int tmode = 0;
-            if (WALLY) tmode = (gyr == 0) ? 1 : ((gyr == ny - 1) ? -1 : 0);
-            recon_face<Real, COUPLED, true, RS>(rec, L, Rr, S::HX1, tmode, ph.h, fb, gb);
+            const int L = (fy + H) * S::HX1 + fx + H - 1, Rr = L + 1;
+            if (UPW) {
+                recon_face_upwind<Real, COUPLED, true, RS>(rec, L, Rr, 1, S::HX1, ph.h, fb, gb);
+            } else {
+                int tmode = 0;
+                if (WALLY) tmode = (gyr == 0) ? 1 : ((gyr == ny - 1) ? -1 : 0);
+                recon_face<Real, COUPLED, true, RS>(rec, L, Rr, S::HX1, tmode, ph.h, fb, gb);
+            }
             ld4(aux + L * AS, au);
             ld4(aux + Rr * AS, bu);
             ady = S::F64 ? aux[L * AS + 4] : sdy[L];
@@ -866,7 +939,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
             const int fx = u % TX, fy = u / TX;
             const int gyf = y0 + fy;  // face below row gyf
             if (x0 + fx >= nx || gyf - 1 >= ny) continue;
-            const int D = fy * S::HX1 + fx + 1, U = D + S::HX1;
+            const int D = (fy + H - 1) * S::HX1 + fx + H, U = D + S::HX1;
             if (WALLY && (gyf == 0 || gyf == ny)) {
                 const bool top = (gyf == ny);
                 const int c0 = top ? D : U;
@@ -877,7 +950,8 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
                 ld4(aux + c0 * AS, au);
                 face_flux<Real, COUPLED, false>(ph, fb, gb, au[0], Real(0), au[2], au[3], Real(0), true, out);
             } else {
-                recon_face<Real, COUPLED, false, RS>(rec, D, U, 1, 0, ph.h, fb, gb);
+                if (UPW) recon_face_upwind<Real, COUPLED, false, RS>(rec, D, U, S::HX1, 1, ph.h, fb, gb);
+                else recon_face<Real, COUPLED, false, RS>(rec, D, U, 1, 0, ph.h, fb, gb);
                 ld4(aux + D * AS, au);
                 ld4(aux + U * AS, bu);
                 ady = S::F64 ? aux[D * AS + 4] : sdy[D];
@@ -955,8 +1029,9 @@ struct InstDesc {
     int use_tma;
 };
 
-template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
-__global__ void __launch_bounds__((TileShape<Real, TX, TY, COUPLED>::NT), (TileShape<Real, TX, TY, COUPLED>::MINB))
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW = false>
+__global__ void __launch_bounds__((TileShape<Real, TX, TY, COUPLED, UPW>::NT),
+                                  (TileShape<Real, TX, TY, COUPLED, UPW>::MINB))
 step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ work) {
     const int2 item = work[blockIdx.x];   // (problem, tile)
     const InstDesc<Real> *d = descs + item.x;
@@ -978,7 +1053,7 @@ step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ w
     a.status = d->status;
     const Phys<Real> &ph = d->ph;   // read-only: reloaded on demand rather than pinned in registers
     const int tx = item.y % d->tiles_x, ty = item.y / d->tiles_x;
-    step_tile<Real, TX, TY, COUPLED, WALLY>(&d->tm_state[cur], &d->tm_hist[cur], a, ph, tx * TX, ty * TY);
+    step_tile<Real, TX, TY, COUPLED, WALLY, UPW>(&d->tm_state[cur], &d->tm_hist[cur], a, ph, tx * TX, ty * TY);
 }
 
 // One step of a single problem.  Tensor maps, arguments and constants arrive
@@ -989,13 +1064,14 @@ step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ w
 #ifndef DUGKS_SOLO_MINB
 #define DUGKS_SOLO_MINB 0   // 0: the occupancy the shared memory allows
 #endif
-template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
-__global__ void __launch_bounds__((TileShape<Real, TX, TY, COUPLED>::NT),
-                                  (DUGKS_SOLO_MINB > 0 ? DUGKS_SOLO_MINB : TileShape<Real, TX, TY, COUPLED>::MINB))
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW = false>
+__global__ void __launch_bounds__((TileShape<Real, TX, TY, COUPLED, UPW>::NT),
+                                  (DUGKS_SOLO_MINB > 0 ? DUGKS_SOLO_MINB : TileShape<Real, TX, TY, COUPLED, UPW>::MINB))
 solo_step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_constant__ CUtensorMap tm_hist,
                  const __grid_constant__ StepArgs<Real> a, const __grid_constant__ Phys<Real> ph, int tiles_x) {
     const int tile = (int)blockIdx.x;
-    step_tile<Real, TX, TY, COUPLED, WALLY>(&tm_state, &tm_hist, a, ph, (tile % tiles_x) * TX, (tile / tiles_x) * TY);
+    step_tile<Real, TX, TY, COUPLED, WALLY, UPW>(&tm_state, &tm_hist, a, ph, (tile % tiles_x) * TX,
+                                                 (tile / tiles_x) * TY);
 }
 
 // After a batched step: every instance's buffers swap and its step count grows.

@@ -18,8 +18,10 @@ template <typename Real> struct FieldArgs;
 template <typename Real> struct InstDesc;
 
 template <typename Real>
-cudaError_t launch_step(int tile, const CUtensorMap &tm_state, const CUtensorMap &tm_hist, const StepArgs<Real> &a,
-                        const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st);
+cudaError_t launch_step(int tile, bool upw, const CUtensorMap &tm_state, const CUtensorMap &tm_hist,
+                        const StepArgs<Real> &a, const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st);
+template <typename Real>
+int step_box_rows(int tile, bool upw);
 template <typename Real>
 int tile_count();
 template <typename Real>
@@ -34,10 +36,10 @@ template <typename Real>
 cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, double p_ref, double *dist,
                           double *hist_out, cudaStream_t st);
 template <typename Real>
-cudaError_t batch_prepare(int tile, bool coupled, bool wally);
+cudaError_t batch_prepare(int tile, bool coupled, bool wally, bool upw);
 template <typename Real>
-cudaError_t launch_batch_step(int tile, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled,
-                              bool wally, cudaStream_t st);
+cudaError_t launch_batch_step(int tile, bool upw, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst,
+                              bool coupled, bool wally, cudaStream_t st);
 cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
                           int have_snap, double *partial, double *out, cudaStream_t st);
 
@@ -58,6 +60,7 @@ struct dugks_ctx {
     dugks::Layout L;
     bool fp32, coupled, wally;
     int tile;   // index of the compiled tile shape the step kernels use
+    bool upw;   // upwind reconstruction (R14) instead of the central one
     cudaStream_t st;
     unsigned char *ws;
     bool owns;

@@ -37,55 +37,72 @@ cudaError_t with_tile(int v, F &&f) {
     }
 }
 
-// Calls f(bool_constant<COUPLED>, bool_constant<WALLY>).
-template <typename F>
-cudaError_t with_variant(bool coupled, bool wally, F &&f) {
+// Calls f(integral_constant<int, tile>, bool_constant<COUPLED>,
+// bool_constant<WALLY>, bool_constant<UPW>) for the compiled kernel variant.
+// The upwind reconstruction is compiled for the default tile shape and
+// periodic boundaries only.
+template <typename Real, typename F>
+cudaError_t with_kernel(int tile, bool coupled, bool wally, bool upw, F &&f) {
     using T = std::true_type;
     using U = std::false_type;
-    if (coupled) return wally ? f(T{}, T{}) : f(T{}, U{});
-    return wally ? f(U{}, T{}) : f(U{}, U{});
+    if (upw) {
+        if (tile != 0 || wally) return cudaErrorInvalidValue;
+        const std::integral_constant<int, 0> v0{};
+        return coupled ? f(v0, T{}, U{}, T{}) : f(v0, U{}, U{}, T{});
+    }
+    return with_tile<Real>(tile, [&](auto v) {
+        if (coupled) return wally ? f(v, T{}, T{}, U{}) : f(v, T{}, U{}, U{});
+        return wally ? f(v, U{}, T{}, U{}) : f(v, U{}, U{}, U{});
+    });
 }
 
-template <typename Real, int TX, int TY, bool COUPLED, bool WALLY>
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 static cudaError_t step_attr_t() {
-    using S = TileShape<Real, TX, TY, COUPLED>;
-    static const cudaError_t attr = cudaFuncSetAttribute(step_kernel<Real, TX, TY, COUPLED, WALLY>,
+    using S = TileShape<Real, TX, TY, COUPLED, UPW>;
+    static const cudaError_t attr = cudaFuncSetAttribute(step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)S::smem_bytes);
-    static const cudaError_t attr_solo = cudaFuncSetAttribute(solo_step_kernel<Real, TX, TY, COUPLED, WALLY>,
+    static const cudaError_t attr_solo = cudaFuncSetAttribute(solo_step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
                                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                               (int)S::smem_bytes);
     return attr != cudaSuccess ? attr : attr_solo;
 }
 
+#define DUGKS_KERNEL_PARAMS(v, c, w, u)                                                                          \
+    constexpr int TX = TileSet<Real>::TX[decltype(v)::value], TY = TileSet<Real>::TY[decltype(v)::value];         \
+    constexpr bool C = decltype(c)::value, W = decltype(w)::value, UP = decltype(u)::value;                       \
+    using S = TileShape<Real, TX, TY, C, UP>;
+
 // Must run outside stream capture (sets the kernels' shared-memory limit).
 template <typename Real>
-cudaError_t step_prepare(int tile, bool coupled, bool wally) {
-    return with_tile<Real>(tile, [&](auto v) {
-        constexpr int TX = TileSet<Real>::TX[decltype(v)::value], TY = TileSet<Real>::TY[decltype(v)::value];
-        return with_variant(coupled, wally, [&](auto c, auto w) {
-            return step_attr_t<Real, TX, TY, decltype(c)::value, decltype(w)::value>();
-        });
+cudaError_t step_prepare(int tile, bool coupled, bool wally, bool upw) {
+    return with_kernel<Real>(tile, coupled, wally, upw, [&](auto v, auto c, auto w, auto u) {
+        DUGKS_KERNEL_PARAMS(v, c, w, u)
+        (void)sizeof(S);
+        return step_attr_t<Real, TX, TY, C, W, UP>();
     });
+}
+
+// Rows of the step kernel's input box (the tensor maps' box height).
+template <typename Real>
+int step_box_rows(int tile, bool upw) {
+    const int ty = (tile >= 0 && tile < TileSet<Real>::N) ? TileSet<Real>::TY[tile] : 0;
+    return ty + (upw ? 6 : 4);
 }
 
 // One step of one problem: maps, arguments and constants by value.
 template <typename Real>
-cudaError_t launch_step(int tile, const CUtensorMap &tm_state, const CUtensorMap &tm_hist, const StepArgs<Real> &a,
-                        const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st) {
-    cudaError_t e = step_prepare<Real>(tile, coupled, wally);
+cudaError_t launch_step(int tile, bool upw, const CUtensorMap &tm_state, const CUtensorMap &tm_hist,
+                        const StepArgs<Real> &a, const Phys<Real> &ph, bool coupled, bool wally, cudaStream_t st) {
+    cudaError_t e = step_prepare<Real>(tile, coupled, wally, upw);
     if (e != cudaSuccess) return e;
-    return with_tile<Real>(tile, [&](auto v) {
-        constexpr int TX = TileSet<Real>::TX[decltype(v)::value], TY = TileSet<Real>::TY[decltype(v)::value];
+    return with_kernel<Real>(tile, coupled, wally, upw, [&](auto v, auto c, auto w, auto u) {
+        DUGKS_KERNEL_PARAMS(v, c, w, u)
         const int tiles_x = (a.nx + TX - 1) / TX;
         const int ntiles = tiles_x * ((a.ny + TY - 1) / TY);
-        return with_variant(coupled, wally, [&](auto c, auto w) {
-            constexpr bool C = decltype(c)::value, W = decltype(w)::value;
-            using S = TileShape<Real, TX, TY, C>;
-            solo_step_kernel<Real, TX, TY, C, W><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph,
+        solo_step_kernel<Real, TX, TY, C, W, UP><<<ntiles, S::NT, S::smem_bytes, st>>>(tm_state, tm_hist, a, ph,
                                                                                         tiles_x);
-            return cudaGetLastError();
-        });
+        return cudaGetLastError();
     });
 }
 
@@ -100,22 +117,18 @@ int tile_dim(int tile, int axis) {
 
 // ---- batched step ----
 template <typename Real>
-cudaError_t batch_prepare(int tile, bool coupled, bool wally) {
-    return step_prepare<Real>(tile, coupled, wally);
+cudaError_t batch_prepare(int tile, bool coupled, bool wally, bool upw) {
+    return step_prepare<Real>(tile, coupled, wally, upw);
 }
 
 template <typename Real>
-cudaError_t launch_batch_step(int tile, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst, bool coupled,
-                              bool wally, cudaStream_t st) {
+cudaError_t launch_batch_step(int tile, bool upw, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst,
+                              bool coupled, bool wally, cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
-    cudaError_t e = with_tile<Real>(tile, [&](auto v) {
-        constexpr int TX = TileSet<Real>::TX[decltype(v)::value], TY = TileSet<Real>::TY[decltype(v)::value];
-        return with_variant(coupled, wally, [&](auto c, auto w) {
-            constexpr bool C = decltype(c)::value, W = decltype(w)::value;
-            using S = TileShape<Real, TX, TY, C>;
-            step_kernel<Real, TX, TY, C, W><<<nwork, S::NT, S::smem_bytes, st>>>(descs, work);
-            return cudaGetLastError();
-        });
+    cudaError_t e = with_kernel<Real>(tile, coupled, wally, upw, [&](auto v, auto c, auto w, auto u) {
+        DUGKS_KERNEL_PARAMS(v, c, w, u)
+        step_kernel<Real, TX, TY, C, W, UP><<<nwork, S::NT, S::smem_bytes, st>>>(descs, work);
+        return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
     advance_kernel<Real><<<(ninst + 127) / 128, 128, 0, st>>>(descs, ninst);
@@ -164,18 +177,19 @@ cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, doub
 }
 
 #define DUGKS_INSTANTIATE(Real)                                                                                     \
-    template cudaError_t launch_step<Real>(int, const CUtensorMap &, const CUtensorMap &, const StepArgs<Real> &,  \
-                                           const Phys<Real> &, bool, bool, cudaStream_t);                          \
+    template cudaError_t launch_step<Real>(int, bool, const CUtensorMap &, const CUtensorMap &,                    \
+                                           const StepArgs<Real> &, const Phys<Real> &, bool, bool, cudaStream_t);  \
     template int tile_count<Real>();                                                                                \
     template int tile_dim<Real>(int, int);                                                                          \
+    template int step_box_rows<Real>(int, bool);                                                                    \
     template cudaError_t launch_init<Real>(const double *, Real *, Real *, int, int, int, long long,                \
                                            const Phys<double> &, bool, bool, cudaStream_t);                         \
     template cudaError_t launch_macros<Real>(const FieldArgs<Real> &, double *, const Phys<double> &, bool, bool,  \
                                              double *, double *, double *, double *, cudaStream_t);                 \
     template cudaError_t launch_export<Real>(const FieldArgs<Real> &, int, double, double, double *, double *,     \
                                              cudaStream_t);                                                        \
-    template cudaError_t batch_prepare<Real>(int, bool, bool);                                                     \
-    template cudaError_t launch_batch_step<Real>(int, InstDesc<Real> *, const int2 *, int, int, bool, bool,        \
+    template cudaError_t batch_prepare<Real>(int, bool, bool, bool);                                               \
+    template cudaError_t launch_batch_step<Real>(int, bool, InstDesc<Real> *, const int2 *, int, int, bool, bool,  \
                                                  cudaStream_t);
 
 }  // namespace dugks

@@ -30,6 +30,7 @@ class DugksParams(ctypes.Structure):
         ("u0x", ctypes.c_double), ("u0y", ctypes.c_double),
         ("velocity_field", ctypes.c_int32), ("reserved2", ctypes.c_int32),
         ("vel_u0", ctypes.c_double), ("vel_length", ctypes.c_double),
+        ("recon", ctypes.c_int32), ("reserved3", ctypes.c_int32),
     ]
 
 
@@ -113,6 +114,7 @@ _ENUM = {
     "bc": {"periodic": 0, "wall": 1},
     "visc": {"reciprocal": 0, "linear": 1},
     "velocity_field": {"uniform": 0, "rotation": 1, "shear": 2, "deformation": 3},
+    "recon": {"central": 0, "upwind": 1},
 }
 
 
@@ -132,6 +134,8 @@ def make_params(cfg):
         setattr(p, k, float(cfg.get(k, 0.0)))
     p.velocity_field = _ENUM["velocity_field"][cfg.get("velocity_field", "uniform")]
     p.reserved2 = 0
+    p.recon = _ENUM["recon"][cfg.get("recon", "central")]
+    p.reserved3 = 0
     if p.precision == 0:
         # the FP64 path keeps absolute distributions unless asked otherwise
         p.phi_ref = float(cfg.get("phi_ref_fp64", 0.0))

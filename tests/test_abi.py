@@ -34,8 +34,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_params_struct_size_matches_header():
-    # 10 int32 fields, 15 doubles, 2 int32 (velocity field, reserved), 2 doubles; no padding
-    assert ctypes.sizeof(solver.DugksParams) == 10 * 4 + 15 * 8 + 2 * 4 + 2 * 8
+    # 10 int32 fields, 15 doubles, 2 int32 (velocity field, reserved), 2 doubles,
+    # 2 int32 (reconstruction, reserved); no padding
+    assert ctypes.sizeof(solver.DugksParams) == 10 * 4 + 15 * 8 + 2 * 4 + 2 * 8 + 2 * 4
 
 
 def test_workspace_bytes_and_validation(lib):
@@ -91,3 +92,21 @@ def test_tile_shapes_and_their_validation(lib):
             assert solver.workspace_bytes(dict(cfg, precision=prec, tile_shape=k)) > 0
         assert solver.workspace_bytes(dict(cfg, precision=prec, tile_shape=len(shapes) + 1)) == 0
         assert solver.workspace_bytes(dict(cfg, precision=prec, tile_shape=-1)) == 0
+
+
+def test_upwind_limits_rejected_without_gpu(lib):
+    """The upwind reconstruction is compiled for periodic boundaries and the
+    default tile shape: other combinations are refused before any device work."""
+    import numpy as np
+
+    cfg, f = workloads.random_state(16, 12, seed=1)
+    phi = np.ascontiguousarray(f["phi0"])
+    dp = ctypes.POINTER(ctypes.c_double)
+    h = ctypes.c_void_p()
+    for bad in (dict(cfg, recon="upwind", bc_y="wall"), dict(cfg, recon="upwind", tile_shape=2)):
+        p = solver.make_params(bad)
+        assert lib.dugks_create(ctypes.byref(p), phi.ctypes.data_as(dp), None, None, None, None, 0, None,
+                                ctypes.byref(h)) == -7
+    p = solver.make_params(cfg)
+    p.recon = 2
+    assert lib.dugks_workspace_bytes(ctypes.byref(p)) == 0

@@ -43,6 +43,8 @@ def problems():
     out.append((dict(cfg, precision="fp32", phi_ref=0.5, tile_shape=4), f))
     cfg, f = W.random_state(33, 40, seed=3)
     out.append((dict(cfg, tile_shape=2), f))
+    cfg, f = W.random_state(45, 21, seed=4)
+    out.append((dict(cfg, recon="upwind"), f))
     return out
 
 
