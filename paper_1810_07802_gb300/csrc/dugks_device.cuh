@@ -258,6 +258,45 @@ __device__ __forceinline__ void g_eq_src(int k, const Pt<Real> &s, const GCoef<R
     src = gam * (edot(k, s.drx, s.dry) - c.udr) + (w + gam) * (edot(k, c.f3x, c.f3y) - c.udf3);
 }
 
+// A combination cb g_eq_k + cc S^g_k (deviation form) of every direction,
+// with the per-point products hoisted:
+//     cb g_eq_k + cc S^g_k = w_k (P + B_k) + (Gamma_k - w_k)(R + A_k + B_k) - delta_k0 P
+//     P = 3 cb p',  R = cb rho,  A_k = cc (xi_k - u).grad rho,  B_k = 3 cc (xi_k - u).F
+template <typename Real>
+struct GLin {
+    Real P, R, ax, ay, a0, bx, by, b0, usq15, ux, uy;
+};
+template <typename Real>
+__device__ __forceinline__ GLin<Real> g_lin(const Pt<Real> &s, Real cb, Real cc) {
+    GLin<Real> g;
+    g.P = Real(3) * cb * s.pd;
+    g.R = cb * s.rho;
+    g.ax = cc * s.drx;
+    g.ay = cc * s.dry;
+    g.a0 = s.ux * g.ax + s.uy * g.ay;
+    const Real c3 = Real(3) * cc;
+    g.bx = c3 * s.Fx;
+    g.by = c3 * s.Fy;
+    g.b0 = s.ux * g.bx + s.uy * g.by;
+    g.usq15 = Real(1.5) * (s.ux * s.ux + s.uy * s.uy);
+    g.ux = s.ux;
+    g.uy = s.uy;
+    return g;
+}
+template <typename Real>
+__device__ __forceinline__ Real g_lin_k(int k, const GLin<Real> &g) {
+    const Real w = wq<Real>(k);
+    if (k == 0) {
+        const Real gam = -w * g.usq15;
+        return w * (g.P - g.b0) - g.P + gam * (g.R - g.a0 - g.b0);
+    }
+    const Real eu = edot(k, g.ux, g.uy);
+    const Real gam = w * (eu * (Real(3) + Real(4.5) * eu) - g.usq15);
+    const Real B = edot(k, g.bx, g.by) - g.b0;
+    const Real A = edot(k, g.ax, g.ay) - g.a0;
+    return w * (g.P + B) + gam * ((g.R + A) + B);
+}
+
 __device__ __forceinline__ int wrap(int x, int n) {
     x %= n;
     return x < 0 ? x + n : x;
@@ -649,15 +688,11 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
     if (COUPLED) {
         const Real inv = rcp_r(Real(2) * s.taug + ph.h);
         const Real a = Real(2) * s.taug * inv, bb = ph.h * inv, c = s.taug * ph.h * inv;
-        const GCoef<Real> gc = g_coef(s);
+        const GLin<Real> gl = g_lin(s, bb, c);
 #pragma unroll
         for (int k = 1; k < 9; k++) {
             const int slot = XFACE ? xslot(k) : yslot(k);
-            if (slot >= 0) {
-                Real eq, src;
-                g_eq_src(k, s, gc, eq, src);
-                out[6 + slot] = a * gb[k] + bb * eq + c * src;
-            }
+            if (slot >= 0) out[6 + slot] = a * gb[k] + g_lin_k(k, gl);
         }
     }
 }
@@ -764,12 +799,10 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
     if (COUPLED) {
         const Real inv = rcp_r(Real(2) * s.taug + ph.dt);
         const Real ca = (Real(2) * s.taug - ph.h) * inv, cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
-        const GCoef<Real> gc = g_coef(s);
+        const GLin<Real> gl = g_lin(s, cb, cc);
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            Real eq, src;
-            g_eq_src(k, s, gc, eq, src);
-            const Real bp = ca * dg[k] + cb * eq + cc * src;
+            const Real bp = ca * dg[k] + g_lin_k(k, gl);
             r[R::slot(1, k)] = bp;
             if (TILE) tp[9 + k] = Real(4.0 / 3.0) * bp - Real(1.0 / 3.0) * dg[k];
         }
@@ -809,11 +842,32 @@ constexpr long kPollLimit = 1l << 16;
 //   4. the flux update (Eq. 24) of the tile to global
 // ---------------------------------------------------------------------------
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
+__device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0,
+                                             Real *__restrict__ box, Real *__restrict__ sphi, Real *__restrict__ rec,
+                                             Real *__restrict__ aux, Real *__restrict__ sdy);
+
+// Stages the input box [NQ + 2][BY][BX] of the tile at (x0, y0) with plain
+// loads (periodic wrap / wall mirror); no barrier.
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
+__device__ __forceinline__ void stage_plain(const StepArgs<Real> &a, int x0, int y0, Real *__restrict__ box) {
+    using S = TileShape<Real, TX, TY, COUPLED, UPW>;
+    constexpr int BX = S::BX, BXY = S::BXY, H = S::H;
+    for (int e = threadIdx.x; e < (S::NQ + 2) * BXY; e += S::NT) {
+        const int z = e / BXY, r = e - z * BXY, by = r / BX, bx = r - by * BX;
+        const int gx = wrap(x0 - 4 + bx, a.nx);
+        const int gy = map_row<WALLY>(y0 - H - 1 + by, a.ny, true);
+        const long long g = (long long)gy * a.pitch + gx;
+        constexpr int HG = int(S::off_hbox) - S::NQ * BXY;   // alignment gap before the history planes
+        box[(HG != 0 && z >= S::NQ) ? e + HG : e] = z < S::NQ ? a.src[z * a.plane + g] : a.hsrc[(z - S::NQ) * a.plane + g];
+    }
+}
+
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
                                           const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0) {
     static_assert(!(UPW && WALLY), "the upwind reconstruction is defined for periodic boundaries only");
     using S = TileShape<Real, TX, TY, COUPLED, UPW>;
-    constexpr int RS = S::RS, AS = S::AS, FS = S::FS, BX = S::BX, BXY = S::BXY;
+    constexpr int BXY = S::BXY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 128-byte aligned base for the TMA destinations, whatever the runtime gives
     Real *sm = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
@@ -822,14 +876,11 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     Real *rec = sm + S::off_rec;
     Real *aux = sm + S::off_aux;
     Real *sdy = sm + S::off_dy;
-    Real *sfx = sm + S::off_fx;
-    Real *sfy = sm + S::off_fy;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S::off_bar);
     int *staged_ok = reinterpret_cast<int *>(bar + 1);
 
     const int tid = threadIdx.x;
-    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
-    const long long plane = a.plane;
+    const int nx = a.nx, ny = a.ny;
 
     // 0. stage the input box [NQ + 2][BY][BX]
     constexpr int H = S::H;
@@ -856,16 +907,27 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     if (mode == 1) {
         mbar_wait(bar, 0, 1);  // completed phase: makes the TMA writes visible to this thread
     } else {
-        for (int e = tid; e < (S::NQ + 2) * BXY; e += S::NT) {
-            const int z = e / BXY, r = e - z * BXY, by = r / BX, bx = r - by * BX;
-            const int gx = wrap(x0 - 4 + bx, nx);
-            const int gy = map_row<WALLY>(y0 - H - 1 + by, ny, true);
-            const long long g = (long long)gy * pitch + gx;
-            constexpr int HG = int(S::off_hbox) - S::NQ * BXY;   // alignment gap before the history planes
-            box[(HG != 0 && z >= S::NQ) ? e + HG : e] = z < S::NQ ? a.src[z * plane + g] : a.hsrc[(z - S::NQ) * plane + g];
-        }
+        stage_plain<Real, TX, TY, COUPLED, WALLY, UPW>(a, x0, y0, box);
         __syncthreads();
     }
+
+    tile_compute<Real, TX, TY, COUPLED, WALLY, UPW>(a, ph, x0, y0, box, sphi, rec, aux, sdy);
+}
+
+// Phases 1-4 of one tile whose input box is staged at `box` (the face
+// records reuse it); sphi, rec, aux, sdy: the tile's other shared arrays.
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
+__device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0,
+                                             Real *__restrict__ box, Real *__restrict__ sphi, Real *__restrict__ rec,
+                                             Real *__restrict__ aux, Real *__restrict__ sdy) {
+    using S = TileShape<Real, TX, TY, COUPLED, UPW>;
+    constexpr int RS = S::RS, AS = S::AS, FS = S::FS, BX = S::BX, BXY = S::BXY;
+    constexpr int H = S::H;
+    Real *sfx = box + S::off_fx;
+    Real *sfy = box + S::off_fy;
+    const int tid = threadIdx.x;
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const long long plane = a.plane;
 
     // 1. phi' on the halo-(H+1) region
     for (int t = tid; t < S::N2; t += S::NT) {
