@@ -116,6 +116,15 @@ typedef struct dugks_ctx *dugks_handle;
  * invalid.  Used for admission by HBM footprint. */
 size_t dugks_workspace_bytes(const dugks_params *params);
 
+/* Self-check of the bounded device waits (failure detection without a
+ * fault): launches one CTA that waits, with the step kernel's wait function,
+ * on a shared-memory barrier that no copy ever completes, giving up after
+ * max_polls polls (<= 0: the step kernel's own limit, well under a second).
+ * Returns DUGKS_ERR_TIMEOUT when the wait ran out as designed (the CUDA
+ * context stays usable), DUGKS_OK if it unexpectedly completed, or a CUDA
+ * error.  Synchronises cuda_stream; allocates and frees 4 device bytes. */
+dugks_status dugks_check_bounded_wait(int64_t max_polls, void *cuda_stream);
+
 /* Tile shapes the step kernels are compiled for, for one precision: writes
  * up to `cap` (tx, ty) cell counts (tx may be NULL, likewise ty) and returns
  * how many there are (tile_shape k >= 1 selects entry k - 1), or -1 for an

@@ -22,6 +22,19 @@ using dugks::Phys;
 using dugks::StepArgs;
 
 namespace dugks {
+// Self-check of the bounded mbarrier wait the step kernel relies on: one
+// thread arms a barrier for 16 bytes of a copy that is never issued, waits
+// with at most max_polls polls, and records the timeout in *status.  Nothing
+// spins beyond the limit and no copy is left in flight.
+__global__ void wait_probe_kernel(long max_polls, unsigned *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, 16u);
+        if (!mbar_wait(&bar, 0, max_polls)) atomicOr(status, STATUS_TIMEOUT);
+    }
+}
+
 cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
                           int have_snap, double *partial, double *out, cudaStream_t st) {
     reduce_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(phi, ux, uy, snap, n, have_snap, partial);
@@ -453,6 +466,25 @@ dugks_status dugks_destroy(dugks_handle c) {
     }
     delete c;
     return from_cuda(e);
+}
+
+dugks_status dugks_check_bounded_wait(int64_t max_polls, void *cuda_stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long polls = max_polls > 0 ? (long)max_polls : dugks::kPollLimit;
+    unsigned *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned));
+    if (e != cudaSuccess) return from_cuda(e);
+    unsigned h = 0;
+    e = cudaMemsetAsync(d, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        dugks::wait_probe_kernel<<<1, 32, 0, st>>>(polls, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return from_cuda(e);
+    return (h & dugks::STATUS_TIMEOUT) ? DUGKS_ERR_TIMEOUT : DUGKS_OK;
 }
 
 int32_t dugks_tile_shapes(int32_t precision, int32_t *tx, int32_t *ty, int32_t cap) {

@@ -32,7 +32,7 @@ class Request:
 
 
 class Record:
-    __slots__ = ("rid", "kind", "arrival", "admitted", "finished", "cells", "steps", "result")
+    __slots__ = ("rid", "kind", "arrival", "admitted", "finished", "cells", "steps", "result", "error")
 
     def __init__(self, req):
         self.rid, self.kind, self.arrival = req.rid, req.kind, req.arrival
@@ -40,6 +40,7 @@ class Record:
         self.steps = req.steps
         self.admitted = self.finished = None
         self.result = None
+        self.error = None   # set when the problem failed (e.g. a non-finite or non-physical step)
 
     @property
     def latency(self):
@@ -47,14 +48,17 @@ class Record:
 
 
 def summary(records):
-    """Throughput and latency of a finished run (times in seconds)."""
+    """Throughput and latency of a finished run (times in seconds); failed
+    requests are counted apart and left out of the latency figures."""
+    failed = sum(1 for r in records if r.error is not None)
+    records = [r for r in records if r.error is None]
     if not records:
-        return {"solves": 0}
+        return {"solves": 0, "failed": failed}
     lat = np.array([r.latency for r in records])
     t0 = min(r.arrival for r in records)
     t1 = max(r.finished for r in records)
     updates = sum(r.cells * r.steps for r in records)
-    return {"solves": len(records), "solves_per_s": len(records) / (t1 - t0),
+    return {"solves": len(records), "failed": failed, "solves_per_s": len(records) / (t1 - t0),
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3), "makespan_s": t1 - t0,
             "mlups": updates / (t1 - t0) / 1e6}
@@ -150,7 +154,7 @@ class BatchingServer:
                     rec.admitted = self.clock() - t0
                     s = self.make_solver(req)
                     batch.add(s)
-                    active.append([req, rec, s, req.steps, need])
+                    active.append([req, rec, s, req.steps, need, None])
                     used += need
                 if not active:
                     if pending:
@@ -169,7 +173,20 @@ class BatchingServer:
                     inflight = mark
                 else:
                     inflight = None
-                    batch.sync()
+                    for a in self._sync_members(batch, active):
+                        # a failed problem leaves the batch at once; the others go on
+                        req, rec, s = a[0], a[1], a[2]
+                        rec.finished = self.clock() - t0
+                        rec.error = a[5]
+                        batch.remove(s)
+                        try:
+                            s.close()
+                        except Exception:
+                            pass
+                        used -= a[4]
+                        active.remove(a)
+                        done.append(rec)
+                    finished = [a for a in active if a[3] == 0]
                     for a in finished:
                         req, rec, s = a[0], a[1], a[2]
                         res = s.macros()
@@ -189,6 +206,25 @@ class BatchingServer:
                     pass
             batch.close()
         return sorted(done, key=lambda r: r.rid)
+
+    @staticmethod
+    def _sync_members(batch, active):
+        """Waits for the batch; if that reports a failure, asks every member
+        and returns those that failed, each with its error in slot 5."""
+        try:
+            batch.sync()
+            return []
+        except Exception as e:
+            failed = []
+            for a in active:
+                try:
+                    a[2].sync()
+                except Exception as em:
+                    a[5] = str(em)
+                    failed.append(a)
+            if not failed:
+                raise e
+            return failed
 
 
 class SequentialServer:
@@ -217,10 +253,16 @@ class SequentialServer:
             rec = Record(req)
             rec.admitted = self.clock() - t0
             s = self.make_solver(req)
-            s.step(req.steps)
-            res = s.macros()
+            try:
+                s.step(req.steps)
+                res = s.macros()
+                rec.result = res if self.keep_results else None
+            except Exception as e:
+                rec.error = str(e)
             rec.finished = self.clock() - t0
-            rec.result = res if self.keep_results else None
-            s.close()
+            try:
+                s.close()
+            except Exception:
+                pass
             done.append(rec)
         return sorted(done, key=lambda r: r.rid)

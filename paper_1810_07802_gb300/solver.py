@@ -62,6 +62,7 @@ SIGNATURES = {
     "dugks_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "dugks_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "dugks_check_bounded_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
     "dugks_tile_shapes": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "dugks_autotune": (ctypes.c_int, [ctypes.POINTER(DugksParams), _dp, _dp, _dp, _dp, ctypes.c_int32,
@@ -141,6 +142,13 @@ def make_params(cfg):
         p.phi_ref = float(cfg.get("phi_ref_fp64", 0.0))
         p.p_ref = float(cfg.get("p_ref_fp64", 0.0))
     return p
+
+
+def check_bounded_wait(max_polls=0, stream=None):
+    """Runs the bounded-wait self-check; returns the status code (-6 = the
+    wait ran out as designed)."""
+    return int(lib().dugks_check_bounded_wait(int(max_polls),
+                                              ctypes.c_void_p(stream.cuda_stream) if stream is not None else None))
 
 
 def tile_shapes(precision="fp32"):

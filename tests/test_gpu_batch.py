@@ -150,3 +150,27 @@ def test_serving_results_identical_alone_and_in_the_mix(S):
     seq = SequentialServer().run(small)
     for r, q in zip(seq, small):
         assert_round_off(q.cfg, r.result, recs[q.rid].result, q.rid)
+
+
+def test_server_retires_a_failing_problem(S):
+    """A request whose first step is non-physical (phi < -1/999 at density
+    ratio 1000) fails in the batch; the server records its error and every
+    other request completes bit-identical to its batch of one."""
+    from paper_1810_07802_gb300.serve import BatchingServer, Request, summary
+
+    reqs = []
+    for i in range(5):
+        cfg, f = W.random_state(40 + 3 * i, 30, seed=50 + i)
+        reqs.append(Request(i, "ok", cfg, f, 12, 0.0))
+    cfg, f = W.spinodal(N=32)
+    f = dict(f, phi0=np.full((32, 32), -0.01))
+    reqs.append(Request(5, "bad", cfg, f, 12, 0.0))
+    recs = BatchingServer(hbm_budget=4 << 30, max_members=8, chunk=4).run(reqs)
+    assert recs[5].error is not None and "NONPHYSICAL" in recs[5].error
+    for r, q in zip(recs[:5], reqs[:5]):
+        assert r.error is None
+        m0, _ = alone(S, q.cfg, q.fields, q.steps)
+        for k in m0:
+            assert np.array_equal(r.result[k], m0[k]), (q.rid, k)
+    s = summary(recs)
+    assert s["failed"] == 1 and s["solves"] == 5

@@ -305,3 +305,18 @@ def test_upwind_allen_cahn_fp64_and_fp32(S):
         s.step(40)
         g32 = s.macros()
     assert np.abs(g32["phi"] - ref["phi"]).max() <= 2e-5
+
+
+def test_bounded_wait_times_out_and_context_survives(S):
+    """Failure detection without a fault: a kernel waits, with the step
+    kernel's wait function and poll limit, on a barrier nothing completes; it
+    gives up, the host reads DUGKS_ERR_TIMEOUT, and the GPU keeps working."""
+    import time
+
+    t0 = time.perf_counter()
+    assert S.check_bounded_wait() == -6
+    assert time.perf_counter() - t0 < 5.0
+    assert S.check_bounded_wait(max_polls=10) == -6
+    cfg, f = W.random_state(20, 18, seed=3)
+    got, ref, dist, st = run_both(S, cfg, f, 3)
+    assert_parity(got, ref, dist, st, what="after the timeout check")

@@ -161,3 +161,57 @@ def test_autotune_cache_tunes_each_shape_once_and_server_applies_it():
     assert sorted(calls) == sorted(set(calls)) and len(calls) == 5      # 5 distinct shapes
     for rid, shape in seen:
         assert shape == (2 if reqs[rid].cfg["nx"] < 32 else 1)
+
+
+class FailingSolver(FakeSolver):
+    """Reports a device failure (like a non-physical step) once it has run
+    `fail_at` steps."""
+
+    def __init__(self, req, log, fail_at):
+        super().__init__(req, log)
+        self.fail_at = fail_at
+
+    def sync(self):
+        if self.fail_at is not None and self.steps >= self.fail_at:
+            raise RuntimeError("dugks_sync failed: non-physical")
+
+
+class CheckingBatch(FakeBatch):
+    def sync(self):
+        for s in self.members:
+            s.sync()
+
+
+def test_failed_problem_is_retired_and_the_rest_complete():
+    """A problem whose step fails on the device leaves the batch with its
+    error recorded and its memory released; every other request completes
+    with its full step count (failure detection on the host, no GPU)."""
+    clock, log, tracker = Clock(), [], {"max_members": 0}
+    bad = {3: 12, 7: 1}    # rid -> steps after which it fails
+    reqs = make_requests(12)
+    srv = BatchingServer(1 << 40, max_members=6, chunk=5,
+                         solver_factory=lambda r: FailingSolver(r, log, bad.get(r.rid)),
+                         batch_factory=lambda: CheckingBatch(clock, tracker), footprint=footprint,
+                         clock=clock, sleep=clock.sleep)
+    recs = srv.run(reqs)
+    assert len(recs) == 12
+    for r, q in zip(recs, reqs):
+        if q.rid in bad:
+            assert r.error is not None and r.result is None
+        else:
+            assert r.error is None and r.result["steps"] == q.steps
+    s = summary(recs)
+    assert s["failed"] == 2 and s["solves"] == 10
+
+
+def test_sequential_server_records_failures():
+    clock = Clock()
+
+    class Boom(FakeSolver):
+        def step(self, n):
+            raise RuntimeError("dugks_step failed")
+
+    reqs = make_requests(3)
+    recs = SequentialServer(solver_factory=lambda r: Boom(r, []) if r.rid == 1 else FakeSolver(r, []),
+                            clock=clock, sleep=clock.sleep).run(reqs)
+    assert [r.error is None for r in recs] == [True, False, True]
