@@ -17,9 +17,12 @@ namespace dugks {
 // step); the narrower ones suit narrow domains (e.g. Nx = 4 channels) and are
 // candidates for the autotuner.
 template <typename Real> struct TileSet;
+#ifndef DUGKS_TILE_F32_Y0
+#define DUGKS_TILE_F32_Y0 8
+#endif
 template <> struct TileSet<float> {
     static constexpr int N = 4;
-    static constexpr int TX[N] = {32, 16, 8, 4}, TY[N] = {8, 16, 32, 64};
+    static constexpr int TX[N] = {32, 16, 8, 4}, TY[N] = {DUGKS_TILE_F32_Y0, 16, 32, 64};
 };
 template <> struct TileSet<double> {
     static constexpr int N = 3;
