@@ -48,6 +48,14 @@
  *      t_n + h (the time of the face distributions), with face coordinates
  *      taken in [0, nx) x [0, ny) on periodic axes.  The reversing shear
  *      (Eq. 42) changes sign for t >= L0/U0.
+ *  R15 Sampled velocity field (velocity_field 4, the boundary's
+ *      dugks_set_velocity_field): u at cell centres from a [ny][nx] pair of
+ *      arrays (initially the ux0, uy0 given at creation), steady between
+ *      updates; at a face, the normal component from an optional face array
+ *      (x-face i+1/2 of row j at [j][i], y-face below row j at [j][i]), else
+ *      the mean of the two cells, and the tangential component the mean of
+ *      the two cells (as R3 takes face values of cell quantities); wall faces
+ *      keep u = 0.
  *  R14 Upwind reconstruction (recon = 1; Sec. II.B names the upwind scheme
  *      as the alternative to the central one, and Sec. III.A the fix for
  *      its high-Peclet error, without printing it): each of the two cells
@@ -79,6 +87,8 @@ static int opposite(int i) { return i == 0 ? 0 : ((i + 3) % 8) + 1; }
 struct oracle_ctx {
     oracle_params P;
     long n;            /* steps taken */
+    double *vel;       /* velocity_field 4: ux, uy at cells, ux at x-faces, uy at y-faces ([4][ny][nx]) */
+    int vel_faces;     /* the face planes of vel are set (else faces take the mean of their cells) */
     double *f, *g;     /* psi~ : [9][ny][nx] each */
     double *phiu;      /* (phi u)^{n-1} : [2][ny][nx] */
     double *snap;      /* phi, ux, uy at the previous oracle_reduce call */
@@ -322,6 +332,9 @@ static void cell_states(const oracle_ctx *c, point_state *cs)
             double g9[Q];
             for (int i = 0; i < Q; i++) g9[i] = c->g[i * N + k];
             velocity_pressure(g9, 0.5 * dt, s);
+        } else if (P->velocity_field == 4) {
+            s->ux = c->vel[k];
+            s->uy = c->vel[N + k];
         } else {
             prescribed_velocity(P, (double)(k % nx) + 0.5, (double)(k / nx) + 0.5, (double)c->n * dt,
                                 &s->ux, &s->uy);
@@ -337,11 +350,29 @@ static void cell_states(const oracle_ctx *c, point_state *cs)
     free(phi); free(gx); free(gy); free(lp);
 }
 
+/* R15: velocity of the sampled field (velocity_field 4) at a face between
+ * cells ka and kb (axis 0: x-face, 1: y-face; kf the face's index): the
+ * normal component from the face plane when one was given, else the mean of
+ * the two cells; the tangential component the mean of the two cells. */
+static void sampled_face_velocity(const oracle_ctx *c, int axis, long ka, long kb, long kf, double *uf)
+{
+    long N = (long)c->P.nx * c->P.ny;
+    const double *v = c->vel;
+    double ux = 0.5 * (v[ka] + v[kb]), uy = 0.5 * (v[N + ka] + v[N + kb]);
+    if (c->vel_faces) {
+        if (axis == 0) ux = v[2 * N + kf];
+        else uy = v[3 * N + kf];
+    }
+    uf[0] = ux;
+    uf[1] = uy;
+}
+
 /* Face state from the reconstructed psi_bar and the face means of grad phi,
  * lap phi and d_t(phi u) (R3), then the original distributions (Eq. 28). */
 static void face_distributions(const oracle_ctx *c, const double *fbar, const double *gbar,
                                double dphix, double dphiy, double lap, double Dx, double Dy,
-                               int wall_face, double xf, double yf, double *fpsi, double *gpsi)
+                               int wall_face, double xf, double yf, const double *uf,
+                               double *fpsi, double *gpsi)
 {
     const oracle_params *P = &c->P;
     double dt = P->cfl, h = 0.5 * dt;
@@ -368,6 +399,9 @@ static void face_distributions(const oracle_ctx *c, const double *fbar, const do
     } else if (wall_face) {
         s.ux = 0.0;
         s.uy = 0.0;
+    } else if (P->velocity_field == 4) {
+        s.ux = uf[0];
+        s.uy = uf[1];
     } else {
         prescribed_velocity(P, xf, yf, (double)c->n * dt + h, &s.ux, &s.uy);
     }
@@ -568,11 +602,13 @@ static void one_step(oracle_ctx *c)
                 recon_xface(P, fbp, i, j, fb);
                 if (coupled) recon_xface(P, gbp, i, j, gb);
             }
+            double uf[2] = {0.0, 0.0};
+            if (P->velocity_field == 4) sampled_face_velocity(c, 0, kl, kr, kl, uf);
             face_distributions(c, fb, gb,
                                0.5 * (cs[kl].dphix + cs[kr].dphix), 0.5 * (cs[kl].dphiy + cs[kr].dphiy),
                                0.5 * (cs[kl].lap + cs[kr].lap),
                                0.5 * (cs[kl].Dx + cs[kr].Dx), 0.5 * (cs[kl].Dy + cs[kr].Dy),
-                               0, (double)((i + 1) % nx), (double)j + 0.5, fp, gp);
+                               0, (double)((i + 1) % nx), (double)j + 0.5, uf, fp, gp);
             for (int q = 0; q < Q; q++) { fxf[q * N + kl] = fp[q]; gxf[q * N + kl] = gp[q]; }
         }
 
@@ -588,7 +624,7 @@ static void one_step(oracle_ctx *c)
                 recon_wall(P, fbp, i, top, fb);
                 if (coupled) recon_wall(P, gbp, i, top, gb);
                 face_distributions(c, fb, gb, cs[k0].dphix, 0.0, cs[k0].lap, cs[k0].Dx, 0.0,
-                                   1, (double)i + 0.5, (double)j, fp, gp);
+                                   1, (double)i + 0.5, (double)j, NULL, fp, gp);
             } else {
                 int jm = (j - 1 + ny) % ny, jc = j % ny;
                 long kd = (long)jm * nx + i, ku = (long)jc * nx + i;
@@ -599,11 +635,13 @@ static void one_step(oracle_ctx *c)
                     recon_yface(P, fbp, i, jm, jc, fb);
                     if (coupled) recon_yface(P, gbp, i, jm, jc, gb);
                 }
+                double uf[2] = {0.0, 0.0};
+                if (P->velocity_field == 4) sampled_face_velocity(c, 1, kd, ku, kf, uf);
                 face_distributions(c, fb, gb,
                                    0.5 * (cs[kd].dphix + cs[ku].dphix), 0.5 * (cs[kd].dphiy + cs[ku].dphiy),
                                    0.5 * (cs[kd].lap + cs[ku].lap),
                                    0.5 * (cs[kd].Dx + cs[ku].Dx), 0.5 * (cs[kd].Dy + cs[ku].Dy),
-                                   0, (double)i + 0.5, (double)j, fp, gp);
+                                   0, (double)i + 0.5, (double)j, uf, fp, gp);
             }
             for (int q = 0; q < Q; q++) { fyf[q * NF + kf] = fp[q]; gyf[q * NF + kf] = gp[q]; }
         }
@@ -643,9 +681,10 @@ static int params_valid(const oracle_params *P)
     if (P->nx < 3 || P->ny < 3) return 0;
     if (!(P->cfl > 0.0) || !(P->mobility > 0.0) || !(P->width > 0.0)) return 0;
     if (P->model != 0 && P->model != 1) return 0;
-    if (P->velocity_field < 0 || P->velocity_field > 3) return 0;
+    if (P->velocity_field < 0 || P->velocity_field > 4) return 0;
     if (P->recon < 0 || P->recon > 1 || (P->recon == 1 && P->wall_y)) return 0;
-    if (P->model == 1 && P->velocity_field > 0 && (!(P->vel_u0 > 0.0) || !(P->vel_length > 0.0))) return 0;
+    if (P->model == 1 && P->velocity_field >= 1 && P->velocity_field <= 3 &&
+        (!(P->vel_u0 > 0.0) || !(P->vel_length > 0.0))) return 0;
     if (P->model == 0) {
         if (!(P->rho_h > 0.0) || !(P->rho_l > 0.0)) return 0;
         if (!(P->mu_h > 0.0) || !(P->mu_l > 0.0)) return 0;
@@ -666,6 +705,14 @@ oracle_ctx *oracle_create(const oracle_params *p, const double *phi0,
     c->g = calloc((size_t)Q * N, sizeof(double));
     c->phiu = calloc((size_t)2 * N, sizeof(double));
     c->snap = calloc((size_t)3 * N, sizeof(double));
+    if (p->model == 1 && p->velocity_field == 4) {
+        /* the sampled field starts as the cell velocity given at creation */
+        c->vel = calloc((size_t)4 * N, sizeof(double));
+        for (long k = 0; k < N; k++) {
+            c->vel[k] = ux0 ? ux0[k] : 0.0;
+            c->vel[N + k] = uy0 ? uy0[k] : 0.0;
+        }
+    }
 
     double *gx = malloc(sizeof(double) * N), *gy = malloc(sizeof(double) * N);
     double *lp = malloc(sizeof(double) * N);
@@ -682,6 +729,9 @@ oracle_ctx *oracle_create(const oracle_params *p, const double *phi0,
             s.ux = ux0 ? ux0[k] : 0.0;
             s.uy = uy0 ? uy0[k] : 0.0;
             s.p = p0 ? p0[k] : 0.0;
+        } else if (p->velocity_field == 4) {
+            s.ux = c->vel[k];
+            s.uy = c->vel[N + k];
         } else {
             prescribed_velocity(p, (double)(k % nx) + 0.5, (double)(k / nx) + 0.5, 0.0, &s.ux, &s.uy);
         }
@@ -702,10 +752,25 @@ oracle_ctx *oracle_create(const oracle_params *p, const double *phi0,
     return c;
 }
 
+int oracle_set_velocity(oracle_ctx *c, const double *ux_cell, const double *uy_cell,
+                        const double *ux_xface, const double *uy_yface)
+{
+    if (!c || !c->vel || !ux_cell || !uy_cell || (!ux_xface) != (!uy_yface)) return 0;
+    long N = (long)c->P.nx * c->P.ny;
+    for (long k = 0; k < N; k++) {
+        c->vel[k] = ux_cell[k];
+        c->vel[N + k] = uy_cell[k];
+        c->vel[2 * N + k] = ux_xface ? ux_xface[k] : 0.0;
+        c->vel[3 * N + k] = uy_yface ? uy_yface[k] : 0.0;
+    }
+    c->vel_faces = ux_xface != NULL;
+    return 1;
+}
+
 void oracle_destroy(oracle_ctx *c)
 {
     if (!c) return;
-    free(c->f); free(c->g); free(c->phiu); free(c->snap);
+    free(c->f); free(c->g); free(c->phiu); free(c->snap); free(c->vel);
     free(c);
 }
 

@@ -41,7 +41,8 @@ typedef struct {
     double rho_ref;
     double u0x, u0y;     /* prescribed velocity for model 1, velocity_field 0  */
     int velocity_field;  /* model 1: 0 uniform (u0x, u0y) (Eq. 40); 1 rotation (Eq. 41);
-                            2 reversing shear (Eq. 42); 3 smoothed deformation (Eq. 43) */
+                            2 reversing shear (Eq. 42); 3 smoothed deformation (Eq. 43);
+                            4 sampled arrays (R15; see oracle_set_velocity) */
     int reserved;
     double vel_u0;       /* U0 of fields 1-3                                   */
     double vel_length;   /* L0 of fields 1-3                                   */
@@ -56,6 +57,11 @@ typedef struct oracle_ctx oracle_ctx;
 oracle_ctx *oracle_create(const oracle_params *p, const double *phi0,
                           const double *ux0, const double *uy0, const double *p0);
 void oracle_destroy(oracle_ctx *c);
+/* velocity_field 4: replaces the sampled velocity (R15) for the next steps:
+ * [ny][nx] cell arrays (required) and optional face arrays (both or neither).
+ * Returns 0 if the run has no sampled field or the arguments are invalid. */
+int oracle_set_velocity(oracle_ctx *c, const double *ux_cell, const double *uy_cell,
+                        const double *ux_xface, const double *uy_yface);
 void oracle_step(oracle_ctx *c, long nsteps);
 long oracle_step_count(const oracle_ctx *c);
 /* Cell-centre macros (Eqs. 31-33) of the current state; any pointer may be NULL. */

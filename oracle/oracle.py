@@ -34,7 +34,7 @@ class OracleParams(ctypes.Structure):
 
 _MODEL = {"coupled": 0, "ac": 1}
 _VISC = {"reciprocal": 0, "linear": 1}
-_FIELD = {"uniform": 0, "rotation": 1, "shear": 2, "deformation": 3}
+_FIELD = {"uniform": 0, "rotation": 1, "shear": 2, "deformation": 3, "sampled": 4}
 _RECON = {"central": 0, "upwind": 1}
 
 _lib = None
@@ -64,6 +64,8 @@ def lib():
         L.oracle_prestep.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
         L.oracle_face_psi.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp]
         L.oracle_grad_lap.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+        L.oracle_set_velocity.restype = ctypes.c_int
+        L.oracle_set_velocity.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
         L.oracle_face_bar.argtypes = [ctypes.POINTER(OracleParams), _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
         _lib = L
     return _lib
@@ -150,6 +152,17 @@ class Oracle:
         g = _f64(g, (Q, self.ny, self.nx))
         h = _f64(phiu_prev, (2, self.ny, self.nx))
         lib().oracle_set_state(self.h, _ptr(f), _ptr(g), _ptr(h), int(step_count))
+
+    def set_velocity(self, ux_cell, uy_cell, ux_xface=None, uy_yface=None):
+        """Sampled velocity field (velocity_field "sampled"): cell arrays and
+        optional normal components at x-faces ([j][i] = face i+1/2 of row j)
+        and y-faces ([j][i] = face below row j)."""
+        shp = (self.ny, self.nx)
+        arrs = [_f64(ux_cell, shp), _f64(uy_cell, shp)] + [None if a is None else _f64(a, shp)
+                                                          for a in (ux_xface, uy_yface)]
+        self._vel = arrs
+        if not lib().oracle_set_velocity(self.h, *[None if a is None else _ptr(a) for a in arrs]):
+            raise ValueError("oracle_set_velocity rejected the arguments")
 
     def reduce(self):
         vals = [ctypes.c_double() for _ in range(4)]
