@@ -98,7 +98,9 @@ typedef struct {
                               about the box centre (Eq. 41); 2 shear reversed at
                               t = L0/U0 (Eq. 42); 3 smoothed deformation with period
                               L0/U0 (Eq. 43).  Evaluated at cell centres at t_n and
-                              at faces at t_n + dt/2                               */
+                              at faces at t_n + dt/2.  4: sampled arrays, steady
+                              between dugks_set_velocity_field calls (initially the
+                              ux0, uy0 given to dugks_create)                      */
     int32_t reserved2;     /* must be 0                                            */
     double vel_u0;         /* U0 > 0 of velocity fields 1-3                        */
     double vel_length;     /* L0 > 0 of velocity fields 1-3                        */
@@ -115,6 +117,19 @@ typedef struct dugks_ctx *dugks_handle;
  * buffers, macro staging, reduction scratch), or 0 if the parameters are
  * invalid.  Used for admission by HBM footprint. */
 size_t dugks_workspace_bytes(const dugks_params *params);
+
+/* Sampled velocity field of the Allen-Cahn-only model (velocity_field 4),
+ * used from the next step on.  ux_cell, uy_cell: [ny][nx] host doubles at
+ * the cell centres (required).  ux_xface: the x-component at x-face i+1/2 of
+ * row j ([j][i], the face between columns i and i+1, periodic) and uy_yface:
+ * the y-component at the y-face below row j ([j][i]); both or neither.  A
+ * face without its array takes the mean of the two cells; the tangential
+ * component is always the mean of the two cells; wall faces keep u = 0.
+ * Stored in the solver's workspace in the storage precision; synchronises the
+ * solver's stream.  DUGKS_ERR_UNSUPPORTED if the solver has no sampled field,
+ * DUGKS_ERR_ARG for missing arrays. */
+dugks_status dugks_set_velocity_field(dugks_handle h, const double *ux_cell, const double *uy_cell,
+                                      const double *ux_xface, const double *uy_yface);
 
 /* Self-check of the bounded device waits (failure detection without a
  * fault): launches one CTA that waits, with the step kernel's wait function,

@@ -14,6 +14,7 @@ struct FieldArgs {
     int nx, ny, pitch;
     long long plane;
     double t;                         // time of the state (prescribed velocity fields)
+    const Real *__restrict__ vel;     // sampled velocity field [4][ny][pitch] (velocity field 4), or null
 };
 
 // phi at cell (x, y) of a [ny][nx] double field, periodic in x, periodic or
@@ -54,6 +55,9 @@ __global__ void init_kernel(const double *__restrict__ in, Real *__restrict__ st
         s.ux = in[N + c];
         s.uy = in[2 * N + c];
         s.pd = in[3 * N + c] - ph.p_ref;
+    } else if (ph.vel_kind == 4) {   // sampled field: the cell velocity given at creation
+        s.ux = in[N + c];
+        s.uy = in[2 * N + c];
     } else {
         prescribed_velocity(ph, double(x) + 0.5, double(y) + 0.5, 0.0, s.ux, s.uy);
     }
@@ -110,6 +114,10 @@ __global__ void macro_kernel(FieldArgs<Real> a, const double *__restrict__ phid,
             if (k) sn += d;
         }
         velocity_pressure(mx, my, sn, ph.half_dt, s);
+    } else if (ph.vel_kind == 4) {
+        s.ux = double(a.vel[g]);
+        s.uy = double(a.vel[a.plane + g]);
+        s.pd = 0.0;
     } else {
         prescribed_velocity(ph, double(x) + 0.5, double(y) + 0.5, a.t, s.ux, s.uy);
         s.pd = 0.0;

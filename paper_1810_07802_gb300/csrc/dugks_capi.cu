@@ -66,12 +66,14 @@ bool valid(const dugks_params *p) {
     if (p->bc_y != DUGKS_BC_PERIODIC && p->bc_y != DUGKS_BC_WALL) return false;
     if (p->visc_interp != DUGKS_VISC_RECIPROCAL && p->visc_interp != DUGKS_VISC_LINEAR) return false;
     if (p->gravity_mode != 0 && p->gravity_mode != 1) return false;
-    if (p->velocity_field < 0 || p->velocity_field > 3 || p->reserved2 != 0) return false;
+    if (p->velocity_field < 0 || p->velocity_field > 4 || p->reserved2 != 0) return false;
+    if (p->velocity_field == 4 && p->model != DUGKS_AC_PRESCRIBED_U) return false;
     auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
     auto fin = [](double v) { return std::isfinite(v); };
     if (!pos(p->cfl) || !pos(p->mobility) || !pos(p->width)) return false;
     if (!fin(p->phi_ref) || !fin(p->p_ref) || !fin(p->u0x) || !fin(p->u0y)) return false;
-    if (p->model == DUGKS_AC_PRESCRIBED_U && p->velocity_field > 0 && (!pos(p->vel_u0) || !pos(p->vel_length)))
+    if (p->model == DUGKS_AC_PRESCRIBED_U && p->velocity_field >= 1 && p->velocity_field <= 3 &&
+        (!pos(p->vel_u0) || !pos(p->vel_length)))
         return false;
     if (p->model == DUGKS_COUPLED) {
         if (!pos(p->rho_h) || !pos(p->rho_l) || !pos(p->mu_h) || !pos(p->mu_l)) return false;
@@ -98,6 +100,9 @@ Layout layout(const dugks_params *p) {
         L.off_hist[b] = o;
         o = align_up(o + 2 * L.plane * L.elt, kAlign);
     }
+    L.vel_bytes = (p->model == DUGKS_AC_PRESCRIBED_U && p->velocity_field == 4) ? 4 * L.plane * L.elt : 0;
+    L.off_vel = o;
+    o = align_up(o + L.vel_bytes, kAlign);
     L.off_stage = o;   o = align_up(o + 4 * L.n * sizeof(double), kAlign);
     L.off_phid = o;    o = align_up(o + L.n * sizeof(double), kAlign);
     L.off_snap = o;    o = align_up(o + 3 * L.n * sizeof(double), kAlign);
@@ -146,7 +151,7 @@ Phys<Real> make_phys(const dugks_params &p) {
     ph.u0x = Real(p.u0x);
     ph.u0y = Real(p.u0y);
     ph.vel_kind = p.model == DUGKS_AC_PRESCRIBED_U ? p.velocity_field : 0;
-    if (ph.vel_kind > 0) {
+    if (ph.vel_kind >= 1 && ph.vel_kind <= 3) {
         ph.vel_u = Real(p.vel_u0);
         ph.vel_il = Real(1.0 / p.vel_length);
         ph.vel_ul = Real(p.vel_u0 / p.vel_length);
@@ -222,6 +227,34 @@ cudaError_t run_macros(dugks_ctx *c, double *ophi, double *op, double *oux, doub
 
 }  // namespace
 
+namespace {
+// Uploads the sampled velocity field (R15) as [4][ny][pitch] values of the
+// storage type: cell ux, uy, then the optional face normals (zero if absent).
+template <typename Real>
+cudaError_t upload_velocity_t(dugks_ctx *c, const double *uxc, const double *uyc, const double *uxf,
+                              const double *uyf) {
+    const int nx = c->P.nx, ny = c->P.ny, pitch = c->L.pitch;
+    const size_t plane = c->L.plane;
+    std::vector<Real> h(4 * plane, Real(0));
+    const double *src[4] = {uxc, uyc, uxf, uyf};
+    for (int q = 0; q < 4; q++) {
+        if (!src[q]) continue;
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) h[q * plane + (size_t)y * pitch + x] = Real(src[q][(size_t)y * nx + x]);
+    }
+    cudaError_t e = cudaMemcpyAsync(c->vel(), h.data(), h.size() * sizeof(Real), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e == cudaSuccess) c->vel_faces = uxf ? 1 : 0;
+    return e;
+}
+
+cudaError_t upload_velocity(dugks_ctx *c, const double *uxc, const double *uyc, const double *uxf,
+                            const double *uyf) {
+    return c->fp32 ? upload_velocity_t<float>(c, uxc, uyc, uxf, uyf) : upload_velocity_t<double>(c, uxc, uyc, uxf, uyf);
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t dugks_workspace_bytes(const dugks_params *params) {
@@ -289,7 +322,7 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
     double *in = c->stage();
     const double *src[4] = {phi0, ux0, uy0, p0};
     for (int i = 0; i < 4 && e == cudaSuccess; i++) {
-        if (src[i] && (i == 0 || c->coupled))
+        if (src[i] && (i == 0 || c->coupled || (c->L.vel_bytes && i < 3)))
             e = cudaMemcpyAsync(in + i * L.n, src[i], fb, cudaMemcpyHostToDevice, c->st);
         else
             e = cudaMemsetAsync(in + i * L.n, 0, fb, c->st);
@@ -306,6 +339,11 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
                                            c->wally, c->st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e == cudaSuccess && L.vel_bytes) {
+        // the sampled field starts as the cell velocity given here (zero where none)
+        std::vector<double> zero(ux0 && uy0 ? 0 : L.n, 0.0);
+        e = upload_velocity(c, ux0 ? ux0 : zero.data(), uy0 ? uy0 : zero.data(), nullptr, nullptr);
+    }
     if (e != cudaSuccess) {
         if (c->owns) cudaFree(c->ws);
         delete c;
@@ -466,6 +504,13 @@ dugks_status dugks_destroy(dugks_handle c) {
     }
     delete c;
     return from_cuda(e);
+}
+
+dugks_status dugks_set_velocity_field(dugks_handle c, const double *ux_cell, const double *uy_cell,
+                                      const double *ux_xface, const double *uy_yface) {
+    if (!c || !ux_cell || !uy_cell || (!ux_xface) != (!uy_yface)) return DUGKS_ERR_ARG;
+    if (!c->L.vel_bytes) return DUGKS_ERR_UNSUPPORTED;
+    return from_cuda(upload_velocity(c, ux_cell, uy_cell, ux_xface, uy_yface));
 }
 
 dugks_status dugks_check_bounded_wait(int64_t max_polls, void *cuda_stream) {

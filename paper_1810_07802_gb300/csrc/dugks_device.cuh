@@ -88,7 +88,7 @@ struct Phys {
     Real phi_ref, p_ref;
     Real u0x, u0y;
     int visc_linear, grav_mode;
-    int vel_kind;                 // prescribed field of the A-C-only model (0 uniform)
+    int vel_kind;                 // prescribed field of the A-C-only model (0 uniform, 1-3 analytic, 4 sampled)
     Real vel_u, vel_il, vel_ul;   // U0, 1/L0, U0/L0
     double vel_tr;                // reversal time L0/U0 of the shear field
 };
@@ -105,6 +105,8 @@ struct StepArgs {
     double t_n;                    // time at the start of the step
     int small;                     // grid smaller than a tile plus halo: wrap with %
     int use_tma;                   // tensor maps are valid: interior tiles load by TMA
+    const Real *__restrict__ vel;  // sampled velocity field [4][ny][pitch]: cell ux, uy, x-face ux, y-face uy
+    int vel_faces;                 // the face planes of vel are set (else faces take the mean of their cells)
     unsigned *status;
 };
 
@@ -651,7 +653,7 @@ __device__ __forceinline__ void moments9(const Real g[9], Real &mx, Real &my, Re
 template <typename Real, bool COUPLED, bool XFACE>
 __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9], const Real gb[9], Real dpx,
                                           Real dpy, Real lap, Real Dx, Real Dy, bool wall, Real out[12], Real xf = Real(0),
-                                          Real yf = Real(0), double tf = 0.0) {
+                                          Real yf = Real(0), double tf = 0.0, const Real *uf = nullptr) {
     Pt<Real> s;
     Real sphi = fb[0];
 #pragma unroll
@@ -676,6 +678,9 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
     } else if (wall) {
         s.ux = Real(0);
         s.uy = Real(0);
+    } else if (uf) {   // sampled field, evaluated by the caller
+        s.ux = uf[0];
+        s.uy = uf[1];
     } else {
         prescribed_velocity(ph, xf, yf, tf, s.ux, s.uy);
     }
@@ -771,6 +776,12 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
     } else if (ph.vel_kind == 0) {
         s.ux = ph.u0x;
         s.uy = ph.u0y;
+    } else if (ph.vel_kind == 4) {
+        const int gx = a.small ? wrap(x0 + hx - H, a.nx) : wrap1(x0 + hx - H, a.nx);
+        const int gy = WALLY ? yraw : (a.small ? wrap(yraw, a.ny) : wrap1(yraw, a.ny));
+        const long long gv = (long long)gy * a.pitch + gx;
+        s.ux = a.vel[gv];
+        s.uy = a.vel[a.plane + gv];
     } else {
         const int gx = a.small ? wrap(x0 + hx - H, a.nx) : wrap1(x0 + hx - H, a.nx);
         const int gy = WALLY ? yraw : (a.small ? wrap(yraw, a.ny) : wrap1(yraw, a.ny));
@@ -992,9 +1003,17 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
             bdy = S::F64 ? aux[Rr * AS + 4] : sdy[Rr];
             const Real hf = Real(0.5);
             const int gxf = x0 + fx >= nx ? x0 + fx - nx : x0 + fx;   // face coordinate in [0, nx)
+            Real uf[2];
+            if (!COUPLED && ph.vel_kind == 4) {   // R15: face i+1/2 of row gyr between columns gxl and gxf
+                const int gxl = x0 + fx - 1 < 0 ? x0 + fx - 1 + nx : x0 + fx - 1;
+                const long long kl = (long long)gyr * pitch + gxl, kr = (long long)gyr * pitch + gxf;
+                uf[0] = a.vel_faces ? a.vel[2 * plane + kl] : hf * (a.vel[kl] + a.vel[kr]);
+                uf[1] = hf * (a.vel[plane + kl] + a.vel[plane + kr]);
+            }
             face_flux<Real, COUPLED, true>(ph, fb, gb, hf * (au[0] + bu[0]), hf * (au[1] + bu[1]), hf * (au[2] + bu[2]),
                                            hf * (au[3] + bu[3]), hf * (ady + bdy), false, out, Real(gxf),
-                                           Real(gyr) + Real(0.5), a.t_n + double(ph.h));
+                                           Real(gyr) + Real(0.5), a.t_n + double(ph.h),
+                                           (!COUPLED && ph.vel_kind == 4) ? uf : nullptr);
             store_flux<Real, COUPLED, FS>(sfx + t * FS, out);
         } else {
             const int u = t - S::NFXP;
@@ -1020,9 +1039,17 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
                 bdy = S::F64 ? aux[U * AS + 4] : sdy[U];
                 const Real hf = Real(0.5);
                 const int gyw = (!WALLY && gyf >= ny) ? gyf - ny : gyf;   // face coordinate in [0, ny)
+                Real uf[2];
+                if (!COUPLED && ph.vel_kind == 4) {   // R15: face below row gyw of column x0 + fx
+                    const int gyd = gyw - 1 < 0 ? gyw - 1 + ny : gyw - 1;
+                    const long long kd = (long long)gyd * pitch + x0 + fx, ku = (long long)gyw * pitch + x0 + fx;
+                    uf[0] = hf * (a.vel[kd] + a.vel[ku]);
+                    uf[1] = a.vel_faces ? a.vel[3 * plane + ku] : hf * (a.vel[plane + kd] + a.vel[plane + ku]);
+                }
                 face_flux<Real, COUPLED, false>(ph, fb, gb, hf * (au[0] + bu[0]), hf * (au[1] + bu[1]),
                                                 hf * (au[2] + bu[2]), hf * (au[3] + bu[3]), hf * (ady + bdy), false, out,
-                                                Real(x0 + fx) + Real(0.5), Real(gyw), a.t_n + double(ph.h));
+                                                Real(x0 + fx) + Real(0.5), Real(gyw), a.t_n + double(ph.h),
+                                                (!COUPLED && ph.vel_kind == 4) ? uf : nullptr);
             }
             store_flux<Real, COUPLED, FS>(sfy + u * FS, out);
         }
@@ -1089,6 +1116,8 @@ struct InstDesc {
     int nx, ny, pitch, tiles_x;
     int cur;                               // buffer holding psi~^n (batched use)
     int use_tma;
+    const Real *vel;                       // sampled velocity field, or null
+    int vel_faces;
 };
 
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW = false>
@@ -1112,6 +1141,8 @@ step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ w
     a.t_n = double(steps) * double(d->ph.dt);
     a.small = (a.nx < TX + 4 || a.ny < TY + 4) ? 1 : 0;
     a.use_tma = d->use_tma;
+    a.vel = d->vel;
+    a.vel_faces = d->vel_faces;
     a.status = d->status;
     const Phys<Real> &ph = d->ph;   // read-only: reloaded on demand rather than pinned in registers
     const int tx = item.y % d->tiles_x, ty = item.y / d->tiles_x;

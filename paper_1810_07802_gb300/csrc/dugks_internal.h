@@ -48,7 +48,8 @@ cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy,
 struct Layout {
     int nq, pitch;
     size_t elt, plane, n;
-    size_t off_state[2], off_hist[2], off_stage, off_phid, off_snap, off_partial, off_redout, off_status;
+    size_t off_state[2], off_hist[2], off_vel, off_stage, off_phid, off_snap, off_partial, off_redout, off_status;
+    size_t vel_bytes;   // sampled velocity field [4][ny][pitch] (0 unless used)
     size_t total;
 };
 
@@ -61,6 +62,7 @@ struct dugks_ctx {
     bool fp32, coupled, wally;
     int tile;   // index of the compiled tile shape the step kernels use
     bool upw;   // upwind reconstruction (R14) instead of the central one
+    int vel_faces;   // sampled velocity field: face planes set
     cudaStream_t st;
     unsigned char *ws;
     bool owns;
@@ -75,6 +77,7 @@ struct dugks_ctx {
 
     void *state(int b) const { return ws + L.off_state[b]; }
     void *hist(int b) const { return ws + L.off_hist[b]; }
+    void *vel() const { return L.vel_bytes ? ws + L.off_vel : nullptr; }
     double *stage() const { return reinterpret_cast<double *>(ws + L.off_stage); }
     double *phid() const { return reinterpret_cast<double *>(ws + L.off_phid); }
     double *snap() const { return reinterpret_cast<double *>(ws + L.off_snap); }
@@ -99,6 +102,8 @@ struct dugks_ctx {
         a.t_n = double(steps) * double(fp32 ? (double)phf.dt : phd.dt);
         a.small = (P.nx < tx + 4 || P.ny < ty + 4) ? 1 : 0;
         a.use_tma = tma_ok ? 1 : 0;
+        a.vel = static_cast<const Real *>(vel());
+        a.vel_faces = vel_faces;
         a.status = status();
         return a;
     }
@@ -113,6 +118,7 @@ struct dugks_ctx {
         a.pitch = L.pitch;
         a.plane = (long long)L.plane;
         a.t = double(steps) * P.cfl;
+        a.vel = static_cast<const Real *>(vel());
         return a;
     }
 };
@@ -138,5 +144,7 @@ inline void fill_desc(InstDesc<Real> *d, const dugks_ctx *c, const Phys<Real> &p
     d->tiles_x = (c->P.nx + tx - 1) / tx;
     d->cur = c->cur;
     d->use_tma = c->tma_ok ? 1 : 0;
+    d->vel = static_cast<const Real *>(c->vel());
+    d->vel_faces = c->vel_faces;
 }
 }  // namespace dugks

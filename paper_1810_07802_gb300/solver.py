@@ -63,6 +63,7 @@ SIGNATURES = {
     "dugks_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_check_bounded_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
+    "dugks_set_velocity_field": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
     "dugks_tile_shapes": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "dugks_autotune": (ctypes.c_int, [ctypes.POINTER(DugksParams), _dp, _dp, _dp, _dp, ctypes.c_int32,
@@ -114,7 +115,7 @@ _ENUM = {
     "precision": {"fp64": 0, "fp32": 1},
     "bc": {"periodic": 0, "wall": 1},
     "visc": {"reciprocal": 0, "linear": 1},
-    "velocity_field": {"uniform": 0, "rotation": 1, "shear": 2, "deformation": 3},
+    "velocity_field": {"uniform": 0, "rotation": 1, "shear": 2, "deformation": 3, "sampled": 4},
     "recon": {"central": 0, "upwind": 1},
 }
 
@@ -282,6 +283,13 @@ class Solver:
     @property
     def step_count(self):
         return int(lib().dugks_step_count(self.h))
+
+    def set_velocity_field(self, ux_cell, uy_cell, ux_xface=None, uy_yface=None):
+        """Sampled velocity field (cfg velocity_field "sampled"): cell arrays and
+        optional face normals, [ny][nx] each; used from the next step on."""
+        shp = (self.ny, self.nx)
+        arrs = [_host(a, shp) for a in (ux_cell, uy_cell, ux_xface, uy_yface)]
+        _check(lib().dugks_set_velocity_field(self.h, *[_ptr(a) for a in arrs]), "dugks_set_velocity_field")
 
     def sync(self):
         _check(lib().dugks_sync(self.h), "dugks_sync")

@@ -45,6 +45,10 @@ def problems():
     out.append((dict(cfg, tile_shape=2), f))
     cfg, f = W.random_state(45, 21, seed=4)
     out.append((dict(cfg, recon="upwind"), f))
+    cfg, f = W.zalesak_disk(L=36, R=12.0, slot=3.0, U=0.04)
+    r = np.random.default_rng(9)
+    out.append((dict(cfg, velocity_field="sampled"),
+                dict(f, ux0=0.02 * r.standard_normal((36, 36)), uy0=0.02 * r.standard_normal((36, 36)))))
     return out
 
 

@@ -320,3 +320,56 @@ def test_bounded_wait_times_out_and_context_survives(S):
     cfg, f = W.random_state(20, 18, seed=3)
     got, ref, dist, st = run_both(S, cfg, f, 3)
     assert_parity(got, ref, dist, st, what="after the timeout check")
+
+
+def _sampled_case(L=40, seed=1):
+    cfg, f = W.zalesak_disk(L=L, R=15.0, slot=4.0, U=0.04)
+    r = np.random.default_rng(seed)
+    ux, uy = 0.02 * r.standard_normal((L, L)), 0.02 * r.standard_normal((L, L))
+    return dict(cfg, velocity_field="sampled"), dict(f, ux0=ux, uy0=uy), ux, uy
+
+
+@pytest.mark.parametrize("bc_y", ["periodic", "wall"])
+def test_sampled_velocity_field_fp64(S, bc_y):
+    """Sampled velocity (dugks_set_velocity_field): the field given at
+    creation, then replaced mid-run by another one with face normals."""
+    cfg, f, ux, uy = _sampled_case()
+    cfg["bc_y"] = bc_y
+    r = np.random.default_rng(7)
+    ux2, uy2 = 0.02 * r.standard_normal(ux.shape), 0.02 * r.standard_normal(ux.shape)
+    uxf, uyf = 0.02 * r.standard_normal(ux.shape), 0.02 * r.standard_normal(ux.shape)
+    with S.Solver(cfg, **f) as s:
+        s.step(5)
+        s.set_velocity_field(ux2, uy2, uxf, uyf)
+        s.step(6)
+        got, dist = s.macros(), s.distributions()
+    o = Oracle(cfg, **f)
+    o.step(5)
+    o.set_velocity(ux2, uy2, uxf, uyf)
+    o.step(6)
+    assert_parity(got, o.macros(), dist, o.state(), what="sampled " + bc_y)
+
+
+def test_sampled_velocity_field_fp32_and_errors(S):
+    """FP32 with a smooth sampled field (Eq. 42's shear at the cell centres;
+    grid-scale random fields amplify FP32 round-off at a sharp step)."""
+    import math
+
+    L, U = 64, 0.04
+    cfg, f = W.shear_elongation(L=L, U=U)
+    c = np.arange(L) + 0.5
+    X, Y = np.meshgrid(c, c)
+    ux = U * math.pi * np.sin(math.pi * X / L) * np.cos(math.pi * Y / L)
+    uy = -U * math.pi * np.cos(math.pi * X / L) * np.sin(math.pi * Y / L)
+    cfg, f = dict(cfg, velocity_field="sampled"), dict(f, ux0=ux, uy0=uy)
+    with S.Solver(dict(cfg, precision="fp32", phi_ref=0.5), **f) as s:
+        s.step(8)
+        got = s.macros()
+    o = Oracle(cfg, **f)
+    o.step(8)
+    assert np.abs(got["phi"] - o.macros()["phi"]).max() <= 2e-5
+    c2, f2 = W.translation_circle(L=16, R=4.0, U=0.02)
+    with S.Solver(c2, **f2) as s:
+        with pytest.raises(S.DugksError) as e:
+            s.set_velocity_field(np.zeros((16, 16)), np.zeros((16, 16)))
+        assert e.value.code == -7
