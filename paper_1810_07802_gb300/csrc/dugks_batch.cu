@@ -7,8 +7,8 @@
 // items; one batched step is one launch per non-empty group plus a tiny
 // launch that swaps every member's ping-pong buffers.  The launches of one
 // step are captured once into a CUDA graph and replayed until membership
-// changes.  The CTAs run exactly the single-problem tile code, so each
-// member's result is identical to stepping it alone.
+// changes (one graph of 16 steps and one of a single step).  A member's
+// result does not depend on what else is in the batch.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -51,11 +51,14 @@ struct dugks_batch_ctx {
     static constexpr int kGroups = 16 * kMaxTiles;
     Group groups[kGroups];   // index: (upw * 8 + fp32 * 4 + coupled * 2 + wally) * kMaxTiles + tile
     bool dirty = true;
-    cudaGraphExec_t exec = nullptr;
+    // CUDA graphs of one step and of kUnroll steps of the current membership
+    static constexpr int kUnroll = 16;
+    cudaGraphExec_t exec = nullptr, exec_k = nullptr;
 
     void drop_graph() {
         if (exec) cudaGraphExecDestroy(exec);
-        exec = nullptr;
+        if (exec_k) cudaGraphExecDestroy(exec_k);
+        exec = exec_k = nullptr;
     }
 
     // Rebuilds the host images (descriptors always, work lists when dirty) and uploads them.
@@ -135,7 +138,8 @@ struct dugks_batch_ctx {
         return cudaSuccess;
     }
 
-    cudaError_t capture() {
+    // Captures `steps` consecutive batched steps into one executable graph.
+    cudaError_t capture(int steps, cudaGraphExec_t *out) {
         for (Group &g : groups) {
             if (g.members.empty()) continue;
             cudaError_t e = g.fp32 ? dugks::batch_prepare<float>(g.tile, g.coupled, g.wally, g.upw)
@@ -145,12 +149,13 @@ struct dugks_batch_ctx {
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        cudaError_t el = enqueue_step();
+        cudaError_t el = cudaSuccess;
+        for (int n = 0; n < steps && el == cudaSuccess; n++) el = enqueue_step();
         e = cudaStreamEndCapture(st, &graph);
         if (el != cudaSuccess) e = el;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
         if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) exec = nullptr;
+        if (e != cudaSuccess) *out = nullptr;
         return e;
     }
 };
@@ -190,8 +195,12 @@ dugks_status dugks_batch_step(dugks_batch b, int64_t nsteps) {
     if (!b || nsteps < 0) return DUGKS_ERR_ARG;
     if (nsteps == 0 || b->members.empty()) return DUGKS_OK;
     cudaError_t e = b->upload();
-    if (e == cudaSuccess && !b->exec) e = b->capture();
-    for (int64_t n = 0; n < nsteps && e == cudaSuccess; n++) e = cudaGraphLaunch(b->exec, b->st);
+    // whole blocks of kUnroll steps as one graph launch each, the rest one step per launch
+    const int64_t blocks = nsteps / dugks_batch_ctx::kUnroll, rest = nsteps % dugks_batch_ctx::kUnroll;
+    if (e == cudaSuccess && blocks > 0 && !b->exec_k) e = b->capture(dugks_batch_ctx::kUnroll, &b->exec_k);
+    if (e == cudaSuccess && rest > 0 && !b->exec) e = b->capture(1, &b->exec);
+    for (int64_t n = 0; n < blocks && e == cudaSuccess; n++) e = cudaGraphLaunch(b->exec_k, b->st);
+    for (int64_t n = 0; n < rest && e == cudaSuccess; n++) e = cudaGraphLaunch(b->exec, b->st);
     if (e != cudaSuccess) return from_cuda(e);
     for (dugks_ctx *c : b->members) {
         c->steps += nsteps;
