@@ -146,9 +146,16 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the step kernel's code with comments and layout removed, so that
+    a profile stays valid across comment-only edits."""
+    import re
+
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        h.update(open(p, "rb").read())
+        text = open(p, encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -21,6 +21,13 @@
 //     directions leaving the fluid or running along the wall are extrapolated
 //     from the adjacent cell, directions entering it bounce back; the wall
 //     face has u = 0 and no normal component of grad phi or d_t(phi u).
+//   * Prescribed velocity of the Allen-Cahn-only model (Eqs. 40-43): at cell
+//     centres at t_n, at face centres at t_n + h, face coordinates on
+//     periodic axes taken in [0, n); or sampled arrays (cells, optional face
+//     normals; otherwise faces take the mean of their two cells).
+//   * Upwind reconstruction (optional, periodic only): each cell of a face
+//     carries a linear profile with van Leer-limited slopes; a direction takes
+//     the profile of the cell it leaves, one along the face the mean of both.
 //
 // Storage: distributions psi~ as deviations d_i = psi~_i - psi_ref_i from the
 // rest state (f: w_i phi_ref; g: (p_ref/RT)(w_i - delta_i0)), structure of
