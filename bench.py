@@ -259,6 +259,8 @@ def run_serving(n=100, rate=50.0):
     """The serving mix (Poiseuille / bubble / spinodal requests, Poisson
     arrivals): continuous batching (FP32-shifted) against one solve at a time
     (FP32 and FP64), and the same requests as one burst."""
+    import numpy as np
+
     from paper_1810_07802_gb300 import workloads as W
     from paper_1810_07802_gb300.serve import AutotuneCache, BatchingServer, Request, SequentialServer, summary
 
@@ -290,6 +292,17 @@ def run_serving(n=100, rate=50.0):
         t_tune += time.perf_counter() - t0
         out[label]["batched_fp32_autotuned"] = keep(summary(BatchingServer(
             budget, max_members=128, chunk=50, keep_results=False, tile_policy=tuner).run(requests("fp32", burst))))
+    # accuracy of the FP32 batched results against FP64 solves of the same requests (untimed sample)
+    sample32 = requests("fp32", True)[:12]
+    sample64 = requests("fp64", True)[:12]
+    r32 = BatchingServer(budget, max_members=128, chunk=50).run(sample32)
+    r64 = SequentialServer().run(sample64)
+    worst = {}
+    for a, b, q in zip(r32, r64, sample32):
+        p32, p64 = a.result["phi"], b.result["phi"]
+        l2 = float(np.sqrt(((p32 - p64) ** 2).sum() / (p64 ** 2).sum()))
+        worst[q.kind] = max(worst.get(q.kind, 0.0), l2)
+    out["fp32_vs_fp64"] = {"requests": len(sample32), "phi_l2_rel_max_by_kind": worst, "budget_phi_l2": 1e-4}
     chosen = {}
     for k, v in tuner.shapes.items():
         chosen["%s %dx%d" % (k[1], k[3], k[4])] = v

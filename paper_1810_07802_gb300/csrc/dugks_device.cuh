@@ -51,9 +51,16 @@ __host__ __device__ constexpr int cy(int k) {
     return (k == 0 || k == 1 || k == 5) ? 0 : ((k == 2 || k == 3 || k == 4) ? 1 : -1);
 }
 __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k + 3) % 8) + 1; }
+// D2Q9 weights (Eq. 14).  In FP32 the diagonal weight is 1/36 rounded down by
+// one unit in the last place, so that the nine FP32 weights sum to exactly 1
+// and no rounding bias enters the phi mass through the equilibria.
 template <typename Real>
 __host__ __device__ constexpr Real wq(int k) {
     return k == 0 ? Real(4) / Real(9) : ((k & 1) ? Real(1) / Real(9) : Real(1) / Real(36));
+}
+template <>
+__host__ __device__ constexpr float wq<float>(int k) {
+    return k == 0 ? 4.0f / 9.0f : ((k & 1) ? 1.0f / 9.0f : 0x1.c71c70p-6f);
 }
 // Flux slots of the directions that cross x-faces (xi_x != 0) and y-faces (xi_y != 0).
 __host__ __device__ constexpr int xslot(int k) {
@@ -806,23 +813,36 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
     if (S::F64) aux[c1 * AS + 4] = s.Dy; else sdy[c1] = s.Dy;
 
     Real r[4 * R::NG];
+    // psi-bar-plus of f (Eq. 29) as a relaxation of d towards the equilibrium
+    // plus the source, bp = d + (pf_b f_eq + pf_c S - pf_b d) (pf_a = 1 - pf_b),
+    // and psi~+ = bp + (bp - d) / 3 (Eq. 30).  The nine bp add up to phi' in
+    // exact arithmetic; the rest direction takes phi' minus the other eight,
+    // so rounding cannot bias the phi mass from step to step.
     const FLin<Real> lf = f_lin(ph, s, ph.pf_b, ph.pf_c);
+    Real bsum = Real(0);
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
+    for (int k = 1; k < 9; k++) {
         const Real d = box[k * BXY + e];
-        const Real bp = ph.pf_a * d + f_lin_k(k, lf);
+        const Real bp = d + (f_lin_k(k, lf) - ph.pf_b * d);
         r[R::slot(0, k)] = bp;
-        if (TILE) tp[k] = Real(4.0 / 3.0) * bp - Real(1.0 / 3.0) * d;
+        bsum += bp;
+        if (TILE) tp[k] = bp + (bp - d) * Real(1.0 / 3.0);
+    }
+    {
+        const Real d = box[e];
+        const Real bp = sphi[c2] - bsum;
+        r[R::slot(0, 0)] = bp;
+        if (TILE) tp[0] = bp + (bp - d) * Real(1.0 / 3.0);
     }
     if (COUPLED) {
         const Real inv = rcp_r(Real(2) * s.taug + ph.dt);
-        const Real ca = (Real(2) * s.taug - ph.h) * inv, cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
+        const Real cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
         const GLin<Real> gl = g_lin(s, cb, cc);
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            const Real bp = ca * dg[k] + g_lin_k(k, gl);
+            const Real bp = dg[k] + (g_lin_k(k, gl) - cb * dg[k]);   // ca = 1 - cb
             r[R::slot(1, k)] = bp;
-            if (TILE) tp[9 + k] = Real(4.0 / 3.0) * bp - Real(1.0 / 3.0) * dg[k];
+            if (TILE) tp[9 + k] = bp + (bp - dg[k]) * Real(1.0 / 3.0);
         }
     }
 #pragma unroll
@@ -1070,32 +1090,24 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
         if (gx < nx && gy < ny) {
             const long long g = (long long)gy * pitch + gx;
             const Real dt = ph.dt;
-            Real v[12];
+            // Each axis adds dt (psi_in - psi_out): the difference first, so a
+            // cell with equal fluxes on both sides (a flat region) keeps its value.
+            Real v[12], u[12];
             // west (+) and east (-) x-faces
             load_flux<Real, COUPLED, FS>(sfx + (ly * (TX + 1) + lx) * FS, v);
+            load_flux<Real, COUPLED, FS>(sfx + (ly * (TX + 1) + lx + 1) * FS, u);
 #pragma unroll
             for (int q = 0; q < S::NQ; q++) {
                 const int m = q / 9, k = q % 9;
-                if (cx(k) != 0) tp[q] += dt * sgnmul(cx(k), v[6 * m + xslot(k)]);
-            }
-            load_flux<Real, COUPLED, FS>(sfx + (ly * (TX + 1) + lx + 1) * FS, v);
-#pragma unroll
-            for (int q = 0; q < S::NQ; q++) {
-                const int m = q / 9, k = q % 9;
-                if (cx(k) != 0) tp[q] -= dt * sgnmul(cx(k), v[6 * m + xslot(k)]);
+                if (cx(k) != 0) tp[q] += dt * sgnmul(cx(k), v[6 * m + xslot(k)] - u[6 * m + xslot(k)]);
             }
             // south (+) and north (-) y-faces
             load_flux<Real, COUPLED, FS>(sfy + (ly * TX + lx) * FS, v);
+            load_flux<Real, COUPLED, FS>(sfy + ((ly + 1) * TX + lx) * FS, u);
 #pragma unroll
             for (int q = 0; q < S::NQ; q++) {
                 const int m = q / 9, k = q % 9;
-                if (cy(k) != 0) tp[q] += dt * sgnmul(cy(k), v[6 * m + yslot(k)]);
-            }
-            load_flux<Real, COUPLED, FS>(sfy + ((ly + 1) * TX + lx) * FS, v);
-#pragma unroll
-            for (int q = 0; q < S::NQ; q++) {
-                const int m = q / 9, k = q % 9;
-                if (cy(k) != 0) tp[q] -= dt * sgnmul(cy(k), v[6 * m + yslot(k)]);
+                if (cy(k) != 0) tp[q] += dt * sgnmul(cy(k), v[6 * m + yslot(k)] - u[6 * m + yslot(k)]);
             }
 #pragma unroll
             for (int q = 0; q < S::NQ; q++) a.dst[q * plane + g] = tp[q];
