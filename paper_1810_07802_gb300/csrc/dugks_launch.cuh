@@ -7,6 +7,7 @@
 #include "dugks_aux.cuh"
 #include "dugks_internal.h"
 
+#include <mutex>
 #include <type_traits>
 
 namespace dugks {
@@ -59,16 +60,26 @@ cudaError_t with_kernel(int tile, bool coupled, bool wally, bool upw, F &&f) {
     });
 }
 
+// Raises the step kernels' dynamic shared-memory limit, once per device (the
+// attribute belongs to the device's context).
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 static cudaError_t step_attr_t() {
     using S = TileShape<Real, TX, TY, COUPLED, UPW>;
-    static const cudaError_t attr = cudaFuncSetAttribute(step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)S::smem_bytes);
-    static const cudaError_t attr_solo = cudaFuncSetAttribute(solo_step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
-                                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                              (int)S::smem_bytes);
-    return attr != cudaSuccess ? attr : attr_solo;
+    constexpr int kDevices = 64;
+    static std::once_flag once[kDevices];
+    static cudaError_t result[kDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevices) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [&] {
+        cudaError_t a = cudaFuncSetAttribute(step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
+        cudaError_t b = cudaFuncSetAttribute(solo_step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
+        result[dev] = a != cudaSuccess ? a : b;
+    });
+    return result[dev];
 }
 
 #define DUGKS_KERNEL_PARAMS(v, c, w, u)                                                                          \
