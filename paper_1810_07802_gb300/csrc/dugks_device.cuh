@@ -813,34 +813,44 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
     if (S::F64) aux[c1 * AS + 4] = s.Dy; else sdy[c1] = s.Dy;
 
     Real r[4 * R::NG];
-    // psi-bar-plus of f (Eq. 29) as a relaxation of d towards the equilibrium
-    // plus the source, bp = d + (pf_b f_eq + pf_c S - pf_b d) (pf_a = 1 - pf_b),
-    // and psi~+ = bp + (bp - d) / 3 (Eq. 30).  The nine bp add up to phi' in
-    // exact arithmetic; the rest direction takes phi' minus the other eight,
-    // so rounding cannot bias the phi mass from step to step.
+    // psi-bar-plus of f (Eq. 29) and psi~+ = bp + (bp - d) / 3 (Eq. 30).  FP32:
+    // bp is formed as a relaxation of d towards the equilibrium plus the
+    // source, bp = d + (pf_b f_eq + pf_c S - pf_b d) (pf_a = 1 - pf_b), and the
+    // rest direction takes phi' minus the other eight (the nine add up to phi'
+    // in exact arithmetic), so that rounded coefficients cannot bias the phi
+    // mass from step to step.  FP64 rounding is far below any such drift and
+    // keeps the shorter form pf_a d + pf_b f_eq + pf_c S.
     const FLin<Real> lf = f_lin(ph, s, ph.pf_b, ph.pf_c);
-    Real bsum = Real(0);
+    if (!S::F64) {
+        Real bsum = Real(0);
 #pragma unroll
-    for (int k = 1; k < 9; k++) {
-        const Real d = box[k * BXY + e];
-        const Real bp = d + (f_lin_k(k, lf) - ph.pf_b * d);
-        r[R::slot(0, k)] = bp;
-        bsum += bp;
-        if (TILE) tp[k] = bp + (bp - d) * Real(1.0 / 3.0);
-    }
-    {
+        for (int k = 1; k < 9; k++) {
+            const Real d = box[k * BXY + e];
+            const Real bp = d + (f_lin_k(k, lf) - ph.pf_b * d);
+            r[R::slot(0, k)] = bp;
+            bsum += bp;
+            if (TILE) tp[k] = bp + (bp - d) * Real(1.0 / 3.0);
+        }
         const Real d = box[e];
         const Real bp = sphi[c2] - bsum;
         r[R::slot(0, 0)] = bp;
         if (TILE) tp[0] = bp + (bp - d) * Real(1.0 / 3.0);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const Real d = box[k * BXY + e];
+            const Real bp = ph.pf_a * d + f_lin_k(k, lf);
+            r[R::slot(0, k)] = bp;
+            if (TILE) tp[k] = bp + (bp - d) * Real(1.0 / 3.0);
+        }
     }
     if (COUPLED) {
         const Real inv = rcp_r(Real(2) * s.taug + ph.dt);
-        const Real cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
+        const Real ca = (Real(2) * s.taug - ph.h) * inv, cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
         const GLin<Real> gl = g_lin(s, cb, cc);
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            const Real bp = dg[k] + (g_lin_k(k, gl) - cb * dg[k]);   // ca = 1 - cb
+            const Real bp = S::F64 ? ca * dg[k] + g_lin_k(k, gl) : dg[k] + (g_lin_k(k, gl) - cb * dg[k]);
             r[R::slot(1, k)] = bp;
             if (TILE) tp[9 + k] = bp + (bp - dg[k]) * Real(1.0 / 3.0);
         }
