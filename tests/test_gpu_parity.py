@@ -440,3 +440,28 @@ def test_fp32_phi_mass_does_not_drift(S):
             s.step(4000)
             m = s.macros()["phi"].sum()
         assert abs(m - m0) < 1e-6 * m0, (ref, (m - m0) / m0)
+
+
+@pytest.mark.parametrize("precision,N", [("fp64", 16384), ("fp32", 16384)])
+def test_maximum_size_by_periodic_tiling(S, precision, N):
+    """The largest grids: a 16384^2 box (268M cells; the FP64 workspace is
+    86 GB and plane offsets pass 2^32 elements) filled with a 64^2 periodic
+    pattern.  One step of the tiled box must equal one step of the 64^2 box
+    on every cell, so the oracle's 64^2 result checks all 268M cells."""
+    n = 64
+    cfg, f = W.random_state(n, n, seed=64)
+    ref_o = Oracle(cfg, **f)
+    ref_o.step(2)
+    ref = ref_o.macros()
+    reps = N // n
+    big = {k: (None if v is None else np.tile(v, (reps, reps))) for k, v in f.items()}
+    with S.Solver(dict(cfg, nx=N, ny=N, precision=precision, phi_ref=0.5), workspace="library", **big) as s:
+        s.step(2)
+        got = s.macros()
+    del big
+    tol = {"fp64": dict(phi=1e-10, p=1e-10, ux=1e-10, uy=1e-10),
+           "fp32": dict(phi=2e-5, p=1e-5, ux=1e-7, uy=1e-7)}[precision]
+    for k in ("phi", "p", "ux", "uy"):
+        g = got[k].reshape(reps, n, reps, n)
+        err = np.abs(g - ref[k][None, :, None, :]).max()
+        assert err <= tol[k], (precision, k, err)
