@@ -159,24 +159,36 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken from the current kernel source; else None."""
+def profile_values():
+    """Key/value lines of the committed ncu summary of the step kernel, if it
+    was taken from the current kernel source; else {}."""
     try:
         text = open(PROFILE_SUMMARY).read()
     except OSError:
-        return None
+        return {}
     vals = {}
     for line in text.splitlines():
         line = line.strip().lstrip("-* ")
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
-        return None
+    return vals if vals.get("kernel_source_sha256_16") == kernel_source_hash() else {}
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (None if absent or taken from other kernel code)."""
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(profile_values()["dram_bytes_per_launch"])
     except (KeyError, ValueError):
+        return None
+
+
+def profiled_warp_instructions():
+    """Warp instructions per launch of the step kernel (ncu smsp__inst_executed)."""
+    try:
+        return float(profile_values()["smsp__inst_executed"].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
 
 
@@ -357,6 +369,20 @@ def ours(args):
                 "peak_source": peak_src, "kernel": "solo_step_kernel<float,32,8,coupled,periodic>"}
 
     extra = {}
+    # second bound: instruction issue (4 schedulers per SM, one warp instruction per cycle each)
+    winst = profiled_warp_instructions()
+    if winst is not None:
+        import torch
+
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        peak_issue = sms * 4 * mhz * 1e6
+        ach_issue = winst / (secs / args.steps)
+        extra["issue_roofline"] = {"bound": "issue", "achieved": round(ach_issue / 1e9, 1),
+                                   "peak": round(peak_issue / 1e9, 1), "unit": "Gwarp-instr/s",
+                                   "frac": round(ach_issue / peak_issue, 4),
+                                   "warp_instructions_per_launch": winst,
+                                   "peak_source": "%d SMs x 4 schedulers x %g MHz (sampled SM clock)" % (sms, mhz)}
     if not args.no_fp64:
         k64 = max(3, min(args.steps, 40))
         with ClockSampler(dev_index) as clk64:
