@@ -220,13 +220,17 @@ def run_gpu_measure(precision, steps, warmup, world, rank, recon="central"):
         s = S.Solver(cfg, stream=stream, **f)
     s.step(warmup)
     s.sync()
+    mass0 = s.reduce()[0]   # FP64 phi mass on the GPU (outside the timed region)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     secs = time_steps(s, stream, steps)
     s.sync()   # raises if the device status word reports a non-finite or non-physical step
+    mass1, resid_phi, resid_u, umax = s.reduce()
     secs, _ = job_time_and_value(secs, 1, world)
     s.close()
+    cfg["_health"] = {"phi_mass_rel_drift": (mass1 - mass0) / mass0, "resid_phi": resid_phi, "resid_u": resid_u,
+                      "umax": umax, "steps": steps}
     return secs, cfg
 
 
@@ -409,6 +413,7 @@ def ours(args):
             "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64 spinodal field)",
             "config": dict(config_dict("fp32"), parallelism="replicas" if world > 1 else "single GPU"),
+            "health": cfg.get("_health"),
             "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps}
     if rank == 0:
         line["e2e"] = run_e2e(args.steps)

@@ -49,7 +49,10 @@ typedef enum {
     DUGKS_ERR_NONFINITE = -4,    /* a step produced NaN or Inf                 */
     DUGKS_ERR_NONPHYSICAL = -5,  /* a step met rho <= 0 or mu <= 0             */
     DUGKS_ERR_TIMEOUT = -6,      /* reserved for bounded device waits          */
-    DUGKS_ERR_UNSUPPORTED = -7   /* valid request this build does not provide  */
+    DUGKS_ERR_UNSUPPORTED = -7,  /* valid request this build does not provide  */
+    DUGKS_ERR_BOUNDS = -8        /* a bounds-checked build (DUGKS_BOUNDS_CHECK)
+                                    met an out-of-range index; the access was
+                                    skipped                                    */
 } dugks_status;
 
 typedef enum { DUGKS_BC_PERIODIC = 0, DUGKS_BC_WALL = 1 } dugks_bc;

@@ -30,24 +30,36 @@ def _deps():
     return out
 
 
-def _stale():
-    if not os.path.exists(LIB_PATH):
+CHECKED_DIR = os.path.join(BUILD_DIR, "checked")
+CHECKED_LIB_PATH = os.path.join(CHECKED_DIR, LIB_NAME)
+
+
+def _stale(path):
+    if not os.path.exists(path):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(path)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force=False, verbose_ptxas=False):
-    """Compile (if stale) and return the path of the shared library."""
-    if not force and not _stale():
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force=False, verbose_ptxas=False, checked=False):
+    """Compile (if stale) and return the path of the shared library.
+    checked=True builds the bounds-checked variant (DUGKS_BOUNDS_CHECK=1, every
+    step-kernel index checked before use, violations reported as
+    DUGKS_ERR_BOUNDS) into _build/checked/; it is not part of build()'s default
+    output."""
+    out_dir = CHECKED_DIR if checked else BUILD_DIR
+    lib_path = CHECKED_LIB_PATH if checked else LIB_PATH
+    if not force and not _stale(lib_path):
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC] + ARCH
+    if checked:
+        flags += ["-DDUGKS_BOUNDS_CHECK=1"]
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -59,13 +71,13 @@ def build(force=False, verbose_ptxas=False):
     if verbose_ptxas:
         for _, log in results:
             print(log)
-    tmp = LIB_PATH + ".tmp.%d" % os.getpid()
+    tmp = lib_path + ".tmp.%d" % os.getpid()
     cmd = [nvcc(), "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-cudart", "shared"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -16,6 +16,7 @@
 
 #include "dugks.h"
 #include "dugks_internal.h"
+#include "dugks_trace.h"
 
 using dugks::InstDesc;
 using dugks::fill_desc;
@@ -192,6 +193,7 @@ dugks_status dugks_batch_remove(dugks_batch b, dugks_handle h) {
 int32_t dugks_batch_size(dugks_batch b) { return b ? (int32_t)b->members.size() : -1; }
 
 dugks_status dugks_batch_step(dugks_batch b, int64_t nsteps) {
+    dugks::TraceRange trace_("dugks_batch_step");
     if (!b || nsteps < 0) return DUGKS_ERR_ARG;
     if (nsteps == 0 || b->members.empty()) return DUGKS_OK;
     cudaError_t e = b->upload();
@@ -210,6 +212,7 @@ dugks_status dugks_batch_step(dugks_batch b, int64_t nsteps) {
 }
 
 dugks_status dugks_batch_sync(dugks_batch b) {
+    dugks::TraceRange trace_("dugks_batch_sync");
     if (!b) return DUGKS_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return from_cuda(e);

@@ -15,6 +15,7 @@
 #include "dugks_aux.cuh"
 #include "dugks_internal.h"
 #include "dugks_reduce.cuh"
+#include "dugks_trace.h"
 
 using dugks::FieldArgs;
 using dugks::Layout;
@@ -211,6 +212,7 @@ dugks_status sync_status(dugks_ctx *c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return from_cuda(e);
     c->status_seen |= s;
+    if (c->status_seen & dugks::STATUS_BOUNDS) return DUGKS_ERR_BOUNDS;
     if (c->status_seen & dugks::STATUS_TIMEOUT) return DUGKS_ERR_TIMEOUT;
     if (c->status_seen & dugks::STATUS_NONFINITE) return DUGKS_ERR_NONFINITE;
     if (c->status_seen & dugks::STATUS_NONPHYSICAL) return DUGKS_ERR_NONPHYSICAL;
@@ -265,6 +267,7 @@ size_t dugks_workspace_bytes(const dugks_params *params) {
 dugks_status dugks_create(const dugks_params *params, const double *phi0, const double *ux0, const double *uy0,
                           const double *p0, void *device_workspace, size_t ws_bytes, void *cuda_stream,
                           dugks_handle *out) {
+    dugks::TraceRange trace_("dugks_create");
     if (!out) return DUGKS_ERR_ARG;
     *out = nullptr;
     if (!valid(params) || !phi0) return DUGKS_ERR_ARG;
@@ -354,6 +357,7 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
 }
 
 dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
+    dugks::TraceRange trace_("dugks_step");
     if (!c || nsteps < 0) return DUGKS_ERR_ARG;
     for (int64_t n = 0; n < nsteps; n++) {
         cudaError_t e;
@@ -371,6 +375,7 @@ dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
 }
 
 dugks_status dugks_macros(dugks_handle c, double *phi, double *p, double *ux, double *uy, int32_t dst_is_device) {
+    dugks::TraceRange trace_("dugks_macros");
     if (!c) return DUGKS_ERR_ARG;
     cudaError_t e;
     if (dst_is_device) {
@@ -388,6 +393,7 @@ dugks_status dugks_macros(dugks_handle c, double *phi, double *p, double *ux, do
 }
 
 dugks_status dugks_reduce(dugks_handle c, double *phi_mass, double *resid_phi, double *resid_u, double *umax) {
+    dugks::TraceRange trace_("dugks_reduce");
     if (!c) return DUGKS_ERR_ARG;
     double *s = c->stage();
     const size_t n = c->L.n;
@@ -600,6 +606,7 @@ const char *dugks_status_string(dugks_status s) {
     case DUGKS_ERR_NONPHYSICAL: return "non-physical density or viscosity (<= 0)";
     case DUGKS_ERR_TIMEOUT: return "device wait timed out";
     case DUGKS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case DUGKS_ERR_BOUNDS: return "index out of range (bounds-checked build)";
     }
     return "unknown status";
 }

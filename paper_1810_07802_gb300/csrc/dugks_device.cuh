@@ -87,7 +87,25 @@ __device__ __forceinline__ Real edot(int k, Real x, Real y) {
 template <typename Real>
 __device__ __forceinline__ Real eminus(int a, Real u) { return a == 0 ? -u : (a > 0 ? Real(1) - u : Real(-1) - u); }
 
-enum : unsigned { STATUS_NONFINITE = 1u, STATUS_NONPHYSICAL = 2u, STATUS_TIMEOUT = 4u };
+enum : unsigned { STATUS_NONFINITE = 1u, STATUS_NONPHYSICAL = 2u, STATUS_TIMEOUT = 4u, STATUS_BOUNDS = 8u };
+
+// Bounds-checked build (-DDUGKS_BOUNDS_CHECK=1, a stand-in for a memory
+// sanitizer): every computed index of the step kernel is checked before its
+// access; a violation sets STATUS_BOUNDS in the status word (no trap) and
+// the access is skipped.  In the normal build the checks compile away.
+#ifndef DUGKS_BOUNDS_CHECK
+#define DUGKS_BOUNDS_CHECK 0
+#endif
+__device__ __forceinline__ bool in_bounds(bool ok, unsigned *status) {
+#if DUGKS_BOUNDS_CHECK
+    if (!ok) atomicOr(status, STATUS_BOUNDS);
+    return ok;
+#else
+    (void)ok;
+    (void)status;
+    return true;
+#endif
+}
 
 // Constants of one problem, computed once on the host (passed by value).
 template <typename Real>
@@ -766,6 +784,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
     constexpr int H = S::H;
     const int c1 = hy * S::HX1 + hx;
     const int yraw = y0 + hy - H;
+    if (!in_bounds(hx >= 0 && hx < S::HX1 && hy >= 0 && hy < S::HY1, a.status)) return;
     if (WALLY && (yraw < 0 || yraw >= a.ny)) {
         // outside the walls: never read by a face; keep the smem defined
 #pragma unroll
@@ -775,6 +794,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
         return;
     }
     const int e = (hy + 1) * S::BX + hx + 4 - H;
+    if (!in_bounds(e >= 0 && e < BXY && hx + 4 - H >= 1 && hx + 5 - H < S::BX, a.status)) return;
     Pt<Real> s;
     const int c2 = (hy + 1) * S::HX2 + (hx + 1);
     phi_stencils(sphi, c2, S::HX2, s.dpx, s.dpy, s.lap);
@@ -861,7 +881,8 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
 #pragma unroll
     for (int G = 0; G < R::NG; G++) st4(rec + c1 * RS + 4 * G, r[4 * G], r[4 * G + 1], r[4 * G + 2], r[4 * G + 3]);
 
-    if (TILE && x0 + hx - H < a.nx && yraw < a.ny) {
+    if (TILE && x0 + hx - H < a.nx && yraw < a.ny &&
+        in_bounds(x0 + hx - H >= 0 && yraw >= 0, a.status)) {
         const long long g = (long long)yraw * a.pitch + (x0 + hx - H);
         a.hdst[g] = phux;
         a.hdst[a.plane + g] = phuy;
@@ -904,6 +925,7 @@ __device__ __forceinline__ void stage_plain(const StepArgs<Real> &a, int x0, int
         const int z = e / BXY, r = e - z * BXY, by = r / BX, bx = r - by * BX;
         const int gx = wrap(x0 - 4 + bx, a.nx);
         const int gy = map_row<WALLY>(y0 - H - 1 + by, a.ny, true);
+        if (!in_bounds(gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny, a.status)) continue;
         const long long g = (long long)gy * a.pitch + gx;
         constexpr int HG = int(S::off_hbox) - S::NQ * BXY;   // alignment gap before the history planes
         box[(HG != 0 && z >= S::NQ) ? e + HG : e] = z < S::NQ ? a.src[z * a.plane + g] : a.hsrc[(z - S::NQ) * a.plane + g];
@@ -1027,6 +1049,10 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
             const int gyr = y0 + fy;
             if (gyr >= ny || x0 + fx - 1 >= nx) continue;
             const int L = (fy + H) * S::HX1 + fx + H - 1, Rr = L + 1;
+            // records read: L, Rr and their tangential neighbours (+- one row); upwind also L - 1, Rr + 1
+            if (!in_bounds(L - S::HX1 >= 0 && Rr + S::HX1 < S::N1 && (!UPW || (L - 1 >= 0 && Rr + 1 < S::N1)),
+                           a.status))
+                continue;
             if (UPW) {
                 recon_face_upwind<Real, COUPLED, true, RS>(rec, L, Rr, 1, S::HX1, ph.h, fb, gb);
             } else {
@@ -1044,6 +1070,7 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
             if (!COUPLED && ph.vel_kind == 4) {   // R15: face i+1/2 of row gyr between columns gxl and gxf
                 const int gxl = x0 + fx - 1 < 0 ? x0 + fx - 1 + nx : x0 + fx - 1;
                 const long long kl = (long long)gyr * pitch + gxl, kr = (long long)gyr * pitch + gxf;
+                if (!in_bounds(gxl >= 0 && gxl < nx && gxf >= 0 && gxf < nx && gyr >= 0 && gyr < ny, a.status)) continue;
                 uf[0] = a.vel_faces ? a.vel[2 * plane + kl] : hf * (a.vel[kl] + a.vel[kr]);
                 uf[1] = hf * (a.vel[plane + kl] + a.vel[plane + kr]);
             }
@@ -1058,9 +1085,14 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
             const int gyf = y0 + fy;  // face below row gyf
             if (x0 + fx >= nx || gyf - 1 >= ny) continue;
             const int D = (fy + H - 1) * S::HX1 + fx + H, U = D + S::HX1;
+            // records read: D, U and their tangential neighbours (+- 1); upwind also D - HX1, U + HX1
+            if (!in_bounds(D - 1 >= 0 && U + 1 < S::N1 && (!UPW || (D - S::HX1 >= 0 && U + S::HX1 < S::N1)),
+                           a.status))
+                continue;
             if (WALLY && (gyf == 0 || gyf == ny)) {
                 const bool top = (gyf == ny);
                 const int c0 = top ? D : U;
+                if (!in_bounds(c0 - S::HX1 >= 0 && c0 + S::HX1 < S::N1, a.status)) continue;
                 if (top)
                     recon_wall<Real, COUPLED, true, RS>(rec, c0, -S::HX1, ph.h, fb, gb);
                 else
@@ -1080,6 +1112,7 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
                 if (!COUPLED && ph.vel_kind == 4) {   // R15: face below row gyw of column x0 + fx
                     const int gyd = gyw - 1 < 0 ? gyw - 1 + ny : gyw - 1;
                     const long long kd = (long long)gyd * pitch + x0 + fx, ku = (long long)gyw * pitch + x0 + fx;
+                    if (!in_bounds(gyd >= 0 && gyd < ny && gyw >= 0 && gyw < ny, a.status)) continue;
                     uf[0] = hf * (a.vel[kd] + a.vel[ku]);
                     uf[1] = a.vel_faces ? a.vel[3 * plane + ku] : hf * (a.vel[plane + kd] + a.vel[plane + ku]);
                 }
@@ -1097,7 +1130,7 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
     if (tid < S::NC) {
         const int lx = tid % TX, ly = tid / TX;
         const int gx = x0 + lx, gy = y0 + ly;
-        if (gx < nx && gy < ny) {
+        if (gx < nx && gy < ny && in_bounds(gx >= 0 && gy >= 0 && gx < pitch, a.status)) {
             const long long g = (long long)gy * pitch + gx;
             const Real dt = ph.dt;
             // Each axis adds dt (psi_in - psi_out): the difference first, so a

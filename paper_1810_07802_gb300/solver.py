@@ -36,7 +36,7 @@ class DugksParams(ctypes.Structure):
 
 STATUS = {0: "DUGKS_OK", -1: "DUGKS_ERR_ARG", -2: "DUGKS_ERR_OOM", -3: "DUGKS_ERR_CUDA",
           -4: "DUGKS_ERR_NONFINITE", -5: "DUGKS_ERR_NONPHYSICAL", -6: "DUGKS_ERR_TIMEOUT",
-          -7: "DUGKS_ERR_UNSUPPORTED"}
+          -7: "DUGKS_ERR_UNSUPPORTED", -8: "DUGKS_ERR_BOUNDS"}
 
 # Every symbol include/dugks.h declares, with (restype, argtypes).
 SIGNATURES = {
@@ -88,10 +88,12 @@ def library_path():
 
 
 def lib(build_if_missing=False):
-    """Load the CUDA library.  Raises if it has not been built (no fallback)."""
+    """Load the CUDA library.  Raises if it has not been built (no fallback).
+    DUGKS_LIBRARY in the environment names another build of the same library
+    to load instead (e.g. the bounds-checked one, build.CHECKED_LIB_PATH)."""
     global _lib
     if _lib is None:
-        path = _build.LIB_PATH
+        path = os.environ.get("DUGKS_LIBRARY") or _build.LIB_PATH
         if not os.path.exists(path):
             if not build_if_missing:
                 raise ImportError("CUDA library %s is not built; run __graft_entry__.build()" % path)
