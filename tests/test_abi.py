@@ -110,3 +110,10 @@ def test_upwind_limits_rejected_without_gpu(lib):
     p = solver.make_params(cfg)
     p.recon = 2
     assert lib.dugks_workspace_bytes(ctypes.byref(p)) == 0
+
+
+def test_status_strings_cover_every_code(lib):
+    for code, name in solver.STATUS.items():
+        text = lib.dugks_status_string(code).decode()
+        assert text and text != "unknown status", (code, name)
+    assert lib.dugks_status_string(-99).decode() == "unknown status"
