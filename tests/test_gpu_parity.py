@@ -465,3 +465,45 @@ def test_maximum_size_by_periodic_tiling(S, precision, N):
         g = got[k].reshape(reps, n, reps, n)
         err = np.abs(g - ref[k][None, :, None, :]).max()
         assert err <= tol[k], (precision, k, err)
+
+
+def _rti_positions(phi, L):
+    """Bubble front (light fluid rising at x = 0) and spike tip (heavy fluid
+    falling at x = L/2), as (y - 2L) / L of the phi = 1/2 crossing."""
+    def up(c):          # first crossing from the bottom
+        j = int(np.argmax(c >= 0.5))
+        return j - 1 + (0.5 - c[j - 1]) / (c[j] - c[j - 1]) + 0.5
+    def down(c):        # first crossing from the top
+        j = len(c) - 1 - int(np.argmax(c[::-1] < 0.5))
+        return j + (0.5 - c[j]) / (c[j + 1] - c[j]) + 0.5
+    return (up(phi[:, 0]) - 2 * L) / L, (down(phi[:, L // 2]) - 2 * L) / L
+
+
+def test_rayleigh_taylor_full_size_fp32_tracks_fp64(S):
+    """Sec. IV.D at the paper's size (256 x 1024, At = 0.5, Re = 3000, walls,
+    64,000 steps to t* = 2.5): the bubble rises and the spike falls
+    monotonically, and the FP32-shifted run tracks the FP64 run's positions to
+    1e-3 L; FP64 keeps the phi mass to 1e-10."""
+    L = 256
+    cfg, f = W.rayleigh_taylor(L=L)
+    T = L / 0.04
+    runs = {}
+    for prec in ("fp64", "fp32"):
+        c = dict(cfg, precision=prec, phi_ref=0.5) if prec == "fp32" else dict(cfg)
+        rows, done = [], 0
+        with S.Solver(c, **f) as s:
+            for ts in (0.5, 1.0, 1.5, 2.0, 2.5):
+                n = int(round(ts * T / cfg["cfl"]))
+                s.step(n - done)
+                done = n
+                m = s.macros()
+                rows.append(_rti_positions(m["phi"], L) + (m["phi"].sum(),))
+        runs[prec] = rows
+    b64 = [r[0] for r in runs["fp64"]]
+    s64 = [r[1] for r in runs["fp64"]]
+    assert all(b2 > b1 for b1, b2 in zip(b64, b64[1:])) and b64[0] > 0.1
+    assert all(s2 < s1 for s1, s2 in zip(s64, s64[1:])) and s64[0] < -0.1
+    for r32, r64 in zip(runs["fp32"], runs["fp64"]):
+        assert abs(r32[0] - r64[0]) < 1e-3 and abs(r32[1] - r64[1]) < 1e-3, (r32, r64)
+    m0 = f["phi0"].sum()
+    assert abs(runs["fp64"][-1][2] - m0) < 1e-10 * m0
