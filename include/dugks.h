@@ -221,7 +221,12 @@ dugks_status dugks_destroy(dugks_handle h);
  * launch per kernel variant (precision x model x y-boundary) per step, over a
  * work list of (problem, tile) items, captured once into a CUDA graph and
  * replayed until the membership changes.  Each CTA runs the same tile code as
- * dugks_step, so a member's result is bit-identical to stepping it alone.
+ * dugks_step, with the member's constants read from a device descriptor
+ * instead of the kernel's parameter space, so the two agree to round-off.  A
+ * member of 2048 tiles or more fills the GPU by itself: it is stepped by
+ * dugks_step's kernel on the batch's stream and is bit-identical to stepping
+ * it alone.  Which path a member takes depends on its own size only, so its
+ * result does not depend on the rest of the batch.
  * Members may differ in size, physics and precision.  While a handle is in a
  * batch, advance it only through the batch; its other calls (dugks_macros,
  * dugks_reduce, ...) stay valid but run on the handle's own stream, so use

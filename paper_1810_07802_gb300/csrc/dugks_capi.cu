@@ -42,6 +42,22 @@ cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy,
     reduce_final_kernel<<<1, 32, 0, st>>>(partial, out);
     return cudaGetLastError();
 }
+
+cudaError_t step_on(dugks_ctx *c, long long nsteps, cudaStream_t st) {
+    for (long long n = 0; n < nsteps; n++) {
+        cudaError_t e;
+        if (c->fp32)
+            e = launch_step<float>(c->tile, c->upw, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<float>(),
+                                   c->phf, c->coupled, c->wally, st);
+        else
+            e = launch_step<double>(c->tile, c->upw, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<double>(),
+                                    c->phd, c->coupled, c->wally, st);
+        if (e != cudaSuccess) return e;
+        c->cur ^= 1;
+        c->steps++;
+    }
+    return cudaSuccess;
+}
 }  // namespace dugks
 
 namespace {
@@ -359,19 +375,7 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
 dugks_status dugks_step(dugks_handle c, int64_t nsteps) {
     dugks::TraceRange trace_("dugks_step");
     if (!c || nsteps < 0) return DUGKS_ERR_ARG;
-    for (int64_t n = 0; n < nsteps; n++) {
-        cudaError_t e;
-        if (c->fp32)
-            e = dugks::launch_step<float>(c->tile, c->upw, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<float>(),
-                                          c->phf, c->coupled, c->wally, c->st);
-        else
-            e = dugks::launch_step<double>(c->tile, c->upw, c->tm_state[c->cur], c->tm_hist[c->cur], c->step_args<double>(),
-                                           c->phd, c->coupled, c->wally, c->st);
-        if (e != cudaSuccess) return from_cuda(e);
-        c->cur ^= 1;
-        c->steps++;
-    }
-    return DUGKS_OK;
+    return from_cuda(dugks::step_on(c, nsteps, c->st));
 }
 
 dugks_status dugks_macros(dugks_handle c, double *phi, double *p, double *ux, double *uy, int32_t dst_is_device) {

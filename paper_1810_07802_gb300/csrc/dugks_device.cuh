@@ -932,6 +932,47 @@ __device__ __forceinline__ void stage_plain(const StepArgs<Real> &a, int x0, int
     }
 }
 
+// Stages the cells of an edge tile's box that lie outside the domain
+// (periodic wrap / wall mirror) with plain loads, once TMA has placed the
+// rest of the box (those cells hold its out-of-range fill until overwritten
+// here): whole rows below y = 0 and at y >= ny, then the columns left of
+// x = 0 and at x >= nx in the other rows.  Grids of at least a tile plus
+// halo only (one wrap correction suffices); no barrier.
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
+__device__ __forceinline__ void stage_edges(const StepArgs<Real> &a, int x0, int y0, Real *__restrict__ box) {
+    using S = TileShape<Real, TX, TY, COUPLED, UPW>;
+    constexpr int BX = S::BX, BY = S::BY, BXY = S::BXY, H = S::H;
+    constexpr int HG = int(S::off_hbox) - S::NQ * BXY;   // alignment gap before the history planes
+    const int lc = x0 < 4 ? 4 - x0 : 0;                   // box columns left of x = 0
+    const int rc = max(0, x0 + TX + 4 - a.nx);            // box columns at x >= nx
+    const int tr = max(0, H + 1 - y0);                    // box rows below y = 0
+    const int br = max(0, y0 + TY + H + 1 - a.ny);        // box rows at y >= ny
+    const int nrow = (tr + br) * BX;
+    const int w = lc + rc;
+    const int ncell = nrow + (BY - tr - br) * w;
+    for (int e = threadIdx.x; e < (S::NQ + 2) * ncell; e += S::NT) {
+        const int z = e / ncell, c = e - z * ncell;
+        int bx, by;
+        if (c < nrow) {
+            const int r = c / BX;
+            bx = c - r * BX;
+            by = r < tr ? r : BY - br + (r - tr);
+        } else {
+            const int r = (c - nrow) / w, k = c - nrow - r * w;
+            by = tr + r;
+            bx = k < lc ? k : BX - rc + (k - lc);
+        }
+        const int gx = wrap1(x0 - 4 + bx, a.nx);
+        const int gy = map_row<WALLY>(y0 - H - 1 + by, a.ny, false);
+        if (!in_bounds(gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && bx >= 0 && bx < BX && by >= 0 && by < BY,
+                       a.status))
+            continue;
+        const long long g = (long long)gy * a.pitch + gx;
+        const int b = z * BXY + by * BX + bx;
+        box[(HG != 0 && z >= S::NQ) ? b + HG : b] = z < S::NQ ? a.src[z * a.plane + g] : a.hsrc[(z - S::NQ) * a.plane + g];
+    }
+}
+
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
                                           const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0) {
@@ -952,12 +993,14 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
 
-    // 0. stage the input box [NQ + 2][BY][BX]
+    // 0. stage the input box [NQ + 2][BY][BX]: one TMA load per array (an
+    //    edge tile's out-of-domain cells then overwritten by stage_edges), or
+    //    plain loads throughout on grids smaller than a tile plus halo
     constexpr int H = S::H;
-    const bool interior = a.use_tma && x0 >= 4 && x0 + TX + 4 <= nx && y0 >= H + 1 && y0 + TY + H + 1 <= ny;
+    const bool interior = x0 >= 4 && x0 + TX + 4 <= nx && y0 >= H + 1 && y0 + TY + H + 1 <= ny;
     if (tid == 0) {
         int mode = 0;  // 0: plain loads, 1: staged by TMA, 2: TMA timed out
-        if (interior && !(*((volatile unsigned *)a.status) & STATUS_TIMEOUT)) {
+        if (a.use_tma && !a.small && !(*((volatile unsigned *)a.status) & STATUS_TIMEOUT)) {
             mbar_init(bar, 1);
             mbar_expect_tx(bar, (uint32_t)((S::NQ + 2) * BXY * sizeof(Real)));
             tma_load_3d(box, tm_state_p, x0 - 4, y0 - H - 1, 0, bar);
@@ -976,6 +1019,10 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     if (mode == 2) return;
     if (mode == 1) {
         mbar_wait(bar, 0, 1);  // completed phase: makes the TMA writes visible to this thread
+        if (!interior) {
+            stage_edges<Real, TX, TY, COUPLED, WALLY, UPW>(a, x0, y0, box);
+            __syncthreads();
+        }
     } else {
         stage_plain<Real, TX, TY, COUPLED, WALLY, UPW>(a, x0, y0, box);
         __syncthreads();
@@ -1214,8 +1261,9 @@ step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ w
 // One step of a single problem.  Tensor maps, arguments and constants arrive
 // in the kernel's parameter space, which the arithmetic instructions read as
 // constant-bank operands without occupying registers; the tile code is the
-// same inlined function the batched kernel runs, so a problem gives the same
-// bits stepped alone or in a batch.
+// same inlined function the batched kernel runs (which loads the constants
+// from its descriptor, so the compiler may contract multiply-adds differently
+// and the two agree to round-off).
 #ifndef DUGKS_SOLO_MINB
 #define DUGKS_SOLO_MINB 0   // 0: the occupancy the shared memory allows
 #endif

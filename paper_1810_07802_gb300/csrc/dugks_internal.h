@@ -124,6 +124,11 @@ struct dugks_ctx {
 };
 
 namespace dugks {
+// Enqueues nsteps single-problem steps of c on stream st and advances its
+// step count and ping-pong index (dugks_step on the handle's own stream; a
+// batch's large members on the batch's stream).
+cudaError_t step_on(dugks_ctx *c, long long nsteps, cudaStream_t st);
+
 // Descriptor of one problem for the step kernel (device image built on the host).
 template <typename Real>
 inline void fill_desc(InstDesc<Real> *d, const dugks_ctx *c, const Phys<Real> &ph, int tx) {

@@ -6,7 +6,9 @@ continuous-batching server, it is bit-identical.  The batched kernel and the
 single-problem kernel run the same tile code but are compiled separately
 (constants from a device descriptor vs the parameter space), so the compiler
 may fuse multiply-adds differently: the two paths agree to round-off, and
-both agree with the oracle (test_gpu_parity)."""
+both agree with the oracle (test_gpu_parity).  A member large enough to fill
+the GPU by itself (2048 tiles or more) is stepped by the single-problem kernel
+inside the batch and is bit-identical to stepping it alone."""
 import numpy as np
 import pytest
 
@@ -103,6 +105,53 @@ def test_batch_member_bit_identical_to_batch_of_one(S):
             assert np.array_equal(m[k], m0[k]), (c["nx"], c["ny"], k)
         assert np.array_equal(state, state0)
         assert_round_off(c, m, single_path(S, c, f, 7), (c["nx"], c["ny"]))
+        s.close()
+
+
+def test_large_members_take_the_single_problem_kernel(S):
+    """FP64 512 x 512 (32 x 64 tiles of 16 x 8), FP32 1024 x 512 (32 x 64
+    tiles of 32 x 8) and an upwind FP64 512 x 512 member sit at the 2048-tile
+    threshold: inside a mixed batch each gives the bits of stepping it alone
+    with dugks_step, across a membership change and an odd step count, while
+    the small members keep the bits of their batch of one."""
+    import torch
+
+    big = []
+    cfg, f = W.random_state(512, 512, seed=21)
+    big.append((cfg, f))
+    cfg, f = W.random_state(1024, 512, seed=22, rho_ratio=100.0)
+    big.append((dict(cfg, precision="fp32", phi_ref=0.5), f))
+    cfg, f = W.random_state(512, 512, seed=23)
+    big.append((dict(cfg, recon="upwind"), f))
+    small = problems()[:3]
+    cfg, f = W.random_state(511, 512, seed=24)      # 2048 tiles of the last column ragged
+    edge = (cfg, f)
+    cfg, f = W.random_state(496, 512, seed=25)      # 31 x 64 = 1984 tiles: batched kernel
+    below = (cfg, f)
+    st = torch.cuda.Stream()
+    everyone = big + small + [edge, below]
+    solvers = [S.Solver(c, stream=st, **f) for c, f in everyone]
+    with S.Batch(stream=st) as b:
+        for s in solvers[:-1]:
+            b.add(s)
+        b.step(5)
+        b.remove(solvers[0])
+        b.add(solvers[-1])
+        b.step(18)                  # one graph of 16 steps and two single steps
+        b.sync()
+    want = [5] + [23] * (len(everyone) - 2) + [18]
+    for i, (s, (c, f), n) in enumerate(zip(solvers, everyone, want)):
+        assert s.step_count == n
+        m, state = s.macros(), s.get_state()
+        if i < len(big) or i == len(big) + len(small):
+            with S.Solver(c, **f) as ref:
+                ref.step(n)
+                m0, state0 = ref.macros(), ref.get_state()
+        else:
+            m0, state0 = alone(S, c, f, n)
+        for k in m:
+            assert np.array_equal(m[k], m0[k]), (i, k)
+        assert np.array_equal(state, state0), i
         s.close()
 
 
