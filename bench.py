@@ -30,6 +30,7 @@ FP32_BYTES_PER_CELL = 18 * 4 * 2 + 2 * 4 * 2   # read + write psi~ (18 FP32) and
 FP64_BYTES_PER_CELL = 18 * 8 * 2 + 2 * 8 * 2
 REF_BAND_ROWS = 128
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "solo_step_kernel_fp32_spinodal2048.md")
+PROFILE_SUMMARY_FP64 = os.path.join(ROOT, "profiles", "solo_step_kernel_fp64_spinodal2048.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1810_07802_gb300", "csrc", f)
                   for f in ("dugks_device.cuh", "dugks_launch.cuh")]
 
@@ -159,11 +160,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_values():
-    """Key/value lines of the committed ncu summary of the step kernel, if it
+def profile_values(summary=PROFILE_SUMMARY):
+    """Key/value lines of a committed ncu summary of the step kernel, if it
     was taken from the current kernel source; else {}."""
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(summary).read()
     except OSError:
         return {}
     vals = {}
@@ -188,6 +189,15 @@ def profiled_warp_instructions():
     """Warp instructions per launch of the step kernel (ncu smsp__inst_executed)."""
     try:
         return float(profile_values()["smsp__inst_executed"].split()[0])
+    except (KeyError, ValueError, IndexError):
+        return None
+
+
+def profiled_fp64_flops_per_cell():
+    """Executed FP64 flops per cell update of the FP64 step kernel (ncu: DFMA
+    counted twice, DADD and DMUL once)."""
+    try:
+        return float(profile_values(PROFILE_SUMMARY_FP64)["fp64_flops_per_cell"].split()[0])
     except (KeyError, ValueError, IndexError):
         return None
 
@@ -478,6 +488,20 @@ def ours(args):
                          "ms_per_step": round(secs64 / k64 * 1e3, 4), "hbm_gbs": round(ach64, 1),
                          "hbm_frac": round(ach64 / peak_gbs, 4), "bound": "fp64 alu",
                          "clocks": clk64.summary()}
+        fpc = profiled_fp64_flops_per_cell()
+        if fpc is not None:
+            import torch
+
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            c64 = extra["fp64"]["clocks"]
+            mhz = c64.get("sm_mhz") or c64.get("sm_max_mhz") or 2070.0
+            peak64 = sms * 2 * 2 * mhz * 1e6          # 2 DFMA per cycle per SM, 2 flops each
+            ach = fpc * cells / (secs64 / k64)
+            extra["fp64"]["roofline"] = {"bound": "alu", "achieved": round(ach / 1e9, 1),
+                                         "peak": round(peak64 / 1e9, 1), "unit": "GFLOP/s",
+                                         "frac": round(ach / peak64, 4), "flops_per_cell": fpc,
+                                         "peak_source": "%d SMs x 2 DFMA/cycle x 2 flops x %g MHz (sampled SM "
+                                                        "clock)" % (sms, mhz)}
     if not args.no_upwind:
         # the upwind reconstruction (van Leer slopes) on the same workload, FP32-shifted
         ku = max(3, min(args.steps, 200))
