@@ -41,6 +41,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+// FP32 arithmetic on pairs of lanes (one packed FFMA2 / FADD2 / FMUL2
+// instruction for two values) in the face reconstruction and the cell
+// pre-step; 0 keeps every FP32 operation scalar.  (Packing the face
+// distributions of Eq. 28 as well measured slower on GB300: 0.298 vs 0.288 ms
+// per 2048^2 step, more register moves and spills.)
+#ifndef DUGKS_PACKED_F32
+#define DUGKS_PACKED_F32 1
+#endif
+
 namespace dugks {
 
 // D2Q9 in the paper's order (Eq. 14).  Folded to constants after unrolling.
@@ -164,6 +175,15 @@ __device__ __forceinline__ float cospi_r(float x) { return cospif(x); }
 __device__ __forceinline__ double cospi_r(double x) { return cospi(x); }
 __device__ __forceinline__ bool finite_r(float x) { return isfinite(x); }
 __device__ __forceinline__ bool finite_r(double x) { return isfinite(x); }
+
+// Two FP32 lanes per instruction, each lane rounded as its scalar operation
+// would be (round to nearest).  a - b is fma(-1, b, a), exact like FADD.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(make_float2(-1.0f, -1.0f), b, a); }
 
 // Prescribed velocity of the A-C-only model at (x, y), time t: uniform
 // (Eq. 40), rotation about the box centre (Eq. 41), shear reversed at
@@ -329,6 +349,25 @@ __device__ __forceinline__ Real g_lin_k(int k, const GLin<Real> &g) {
     const Real B = edot(k, g.bx, g.by) - g.b0;
     const Real A = edot(k, g.ax, g.ay) - g.a0;
     return w * (g.P + B) + gam * ((g.R + A) + B);
+}
+
+// Packed FP32 forms for a direction k in 1..4 and its opposite opp(k) = k + 4
+// (lane 0: k, lane 1: opp(k)); xi_opp = -xi_k, so every xi-odd term changes
+// sign between the lanes and each lane repeats its scalar operations.
+template <int K>
+__device__ __forceinline__ float2 f_lin_pair(const FLin<float> &L) {
+    const float e = edot(K, L.Vx, L.Vy);
+    return mul2(f2(wq<float>(K)), add2(f2(L.P), f2(e, -e)));
+}
+template <int K>
+__device__ __forceinline__ float2 g_lin_pair(const GLin<float> &g) {
+    const float w = wq<float>(K);
+    const float eu = edot(K, g.ux, g.uy), eb = edot(K, g.bx, g.by), ea = edot(K, g.ax, g.ay);
+    const float2 eu2 = f2(eu, -eu);
+    const float2 gam = mul2(f2(w), fma2(eu2, fma2(f2(4.5f), eu2, f2(3.0f)), f2(-g.usq15)));
+    const float2 B = sub2(f2(eb, -eb), f2(g.b0));
+    const float2 A = sub2(f2(ea, -ea), f2(g.a0));
+    return fma2(gam, add2(add2(f2(g.R), A), B), mul2(f2(w), add2(f2(g.P), B)));
 }
 
 __device__ __forceinline__ int wrap(int x, int n) {
@@ -544,9 +583,67 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long m
 // records at A +- tstride, B +- tstride: tmode 0 central, +1 one-sided
 // towards +t, -1 one-sided towards -t.  The rest direction of g is not needed
 // by any face quantity and is skipped.
+// FP32 form of recon_face: the two lanes of each half of a record group in
+// one packed instruction; per lane the same operations (T = (n + n') - (s + s'),
+// v = c_a a + c_b b - h c_t T / 4 or / 2).
+template <bool COUPLED, bool XFACE, int RS>
+__device__ __forceinline__ void recon_face_f2(const float *__restrict__ rec, int A, int B, int tstride, int tmode,
+                                              float h, float fb[9], float gb[9]) {
+    const float cp = 0.5f + h, cm = 0.5f - h;
+    const float ht = tmode == 0 ? 0.25f * h : 0.5f * h;
+#pragma unroll
+    for (int G = 0; G < Rec<COUPLED>::NG; G++) {
+        const bool tang = group_tangential<COUPLED, XFACE>(G);
+        const float4 a = *reinterpret_cast<const float4 *>(rec + A * RS + 4 * G);
+        const float4 b = *reinterpret_cast<const float4 *>(rec + B * RS + 4 * G);
+        float4 an = a, bn = b, as = a, bs = b;
+        if (tang) {
+            if (tmode >= 0) {
+                an = *reinterpret_cast<const float4 *>(rec + (A + tstride) * RS + 4 * G);
+                bn = *reinterpret_cast<const float4 *>(rec + (B + tstride) * RS + 4 * G);
+            }
+            if (tmode <= 0) {
+                as = *reinterpret_cast<const float4 *>(rec + (A - tstride) * RS + 4 * G);
+                bs = *reinterpret_cast<const float4 *>(rec + (B - tstride) * RS + 4 * G);
+            }
+        }
+#pragma unroll
+        for (int P = 0; P < 2; P++) {
+            const int s0 = 4 * G + 2 * P, s1 = s0 + 1;
+            const bool n0 = Rec<COUPLED>::used(s0) && !(Rec<COUPLED>::model(s0) == 1 && Rec<COUPLED>::dir(s0) == 0);
+            const bool n1 = Rec<COUPLED>::used(s1) && !(Rec<COUPLED>::model(s1) == 1 && Rec<COUPLED>::dir(s1) == 0);
+            if (!n0 && !n1) continue;
+            const int k0 = Rec<COUPLED>::dir(s0), k1 = Rec<COUPLED>::dir(s1);
+            const int cn0 = XFACE ? cx(k0) : cy(k0), cn1 = XFACE ? cx(k1) : cy(k1);
+            const int ct0 = XFACE ? cy(k0) : cx(k0), ct1 = XFACE ? cy(k1) : cx(k1);
+            const float2 A2 = P == 0 ? f2(a.x, a.y) : f2(a.z, a.w);
+            const float2 B2 = P == 0 ? f2(b.x, b.y) : f2(b.z, b.w);
+            const float2 ca = f2(cn0 == 0 ? 0.5f : (cn0 > 0 ? cp : cm), cn1 == 0 ? 0.5f : (cn1 > 0 ? cp : cm));
+            const float2 cb = f2(cn0 == 0 ? 0.5f : (cn0 > 0 ? cm : cp), cn1 == 0 ? 0.5f : (cn1 > 0 ? cm : cp));
+            float2 V = fma2(cb, B2, mul2(ca, A2));
+            if (tang && (ct0 != 0 || ct1 != 0)) {
+                const float2 Pn = tmode >= 0 ? add2(P == 0 ? f2(an.x, an.y) : f2(an.z, an.w),
+                                                    P == 0 ? f2(bn.x, bn.y) : f2(bn.z, bn.w))
+                                             : add2(A2, B2);
+                const float2 Ps = tmode <= 0 ? add2(P == 0 ? f2(as.x, as.y) : f2(as.z, as.w),
+                                                    P == 0 ? f2(bs.x, bs.y) : f2(bs.z, bs.w))
+                                             : add2(A2, B2);
+                const float2 hv = f2(ct0 > 0 ? -ht : (ct0 < 0 ? ht : 0.0f), ct1 > 0 ? -ht : (ct1 < 0 ? ht : 0.0f));
+                V = fma2(hv, sub2(Pn, Ps), V);
+            }
+            if (n0) { if (Rec<COUPLED>::model(s0) == 0) fb[k0] = V.x; else gb[k0] = V.x; }
+            if (n1) { if (Rec<COUPLED>::model(s1) == 0) fb[k1] = V.y; else gb[k1] = V.y; }
+        }
+    }
+}
+
 template <typename Real, bool COUPLED, bool XFACE, int RS>
 __device__ __forceinline__ void recon_face(const Real *__restrict__ rec, int A, int B, int tstride, int tmode, Real h,
                                            Real fb[9], Real gb[9]) {
+    if constexpr (DUGKS_PACKED_F32 && std::is_same<Real, float>::value) {
+        recon_face_f2<COUPLED, XFACE, RS>(rec, A, B, tstride, tmode, h, fb, gb);
+        return;
+    }
     // value - h xi.slope = (1/2 + h c_n) a + (1/2 - h c_n) b - h c_t s_t
     const Real cp = Real(0.5) + h, cm = Real(0.5) - h;
     const Real ht = tmode == 0 ? Real(0.25) * h : Real(0.5) * h;
@@ -841,7 +938,31 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
     // mass from step to step.  FP64 rounding is far below any such drift and
     // keeps the shorter form pf_a d + pf_b f_eq + pf_c S.
     const FLin<Real> lf = f_lin(ph, s, ph.pf_b, ph.pf_c);
-    if (!S::F64) {
+    if constexpr (DUGKS_PACKED_F32 && !S::F64) {
+        // opposite directions (k, k + 4) in the two lanes of one instruction
+        float2 bsum2 = f2(0.0f);
+        auto fpair = [&](auto kc) {
+            constexpr int K = decltype(kc)::value, O = K + 4;
+            const float2 d = f2(box[K * BXY + e], box[O * BXY + e]);
+            const float2 bp = add2(d, fma2(f2(-ph.pf_b), d, f_lin_pair<K>(lf)));
+            r[R::slot(0, K)] = bp.x;
+            r[R::slot(0, O)] = bp.y;
+            bsum2 = add2(bsum2, bp);
+            if (TILE) {
+                const float2 t = fma2(f2(1.0f / 3.0f), sub2(bp, d), bp);
+                tp[K] = t.x;
+                tp[O] = t.y;
+            }
+        };
+        fpair(std::integral_constant<int, 1>{});
+        fpair(std::integral_constant<int, 2>{});
+        fpair(std::integral_constant<int, 3>{});
+        fpair(std::integral_constant<int, 4>{});
+        const Real d = box[e];
+        const Real bp = sphi[c2] - (bsum2.x + bsum2.y);
+        r[R::slot(0, 0)] = bp;
+        if (TILE) tp[0] = bp + (bp - d) * Real(1.0 / 3.0);
+    } else if (!S::F64) {
         Real bsum = Real(0);
 #pragma unroll
         for (int k = 1; k < 9; k++) {
@@ -868,11 +989,33 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
         const Real inv = rcp_r(Real(2) * s.taug + ph.dt);
         const Real ca = (Real(2) * s.taug - ph.h) * inv, cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
         const GLin<Real> gl = g_lin(s, cb, cc);
+        if constexpr (DUGKS_PACKED_F32 && !S::F64) {
+            auto gpair = [&](auto kc) {
+                constexpr int K = decltype(kc)::value, O = K + 4;
+                const float2 d = f2(dg[K], dg[O]);
+                const float2 bp = add2(d, fma2(f2(-cb), d, g_lin_pair<K>(gl)));
+                r[R::slot(1, K)] = bp.x;
+                r[R::slot(1, O)] = bp.y;
+                if (TILE) {
+                    const float2 t = fma2(f2(1.0f / 3.0f), sub2(bp, d), bp);
+                    tp[9 + K] = t.x;
+                    tp[9 + O] = t.y;
+                }
+            };
+            gpair(std::integral_constant<int, 1>{});
+            gpair(std::integral_constant<int, 2>{});
+            gpair(std::integral_constant<int, 3>{});
+            gpair(std::integral_constant<int, 4>{});
+            const Real bp = dg[0] + (g_lin_k(0, gl) - cb * dg[0]);
+            r[R::slot(1, 0)] = bp;
+            if (TILE) tp[9] = bp + (bp - dg[0]) * Real(1.0 / 3.0);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
-            const Real bp = S::F64 ? ca * dg[k] + g_lin_k(k, gl) : dg[k] + (g_lin_k(k, gl) - cb * dg[k]);
-            r[R::slot(1, k)] = bp;
-            if (TILE) tp[9 + k] = bp + (bp - dg[k]) * Real(1.0 / 3.0);
+            for (int k = 0; k < 9; k++) {
+                const Real bp = S::F64 ? ca * dg[k] + g_lin_k(k, gl) : dg[k] + (g_lin_k(k, gl) - cb * dg[k]);
+                r[R::slot(1, k)] = bp;
+                if (TILE) tp[9 + k] = bp + (bp - dg[k]) * Real(1.0 / 3.0);
+            }
         }
     }
 #pragma unroll
