@@ -1041,10 +1041,11 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
 constexpr long kPollLimit = 1l << 16;
 
 // ---------------------------------------------------------------------------
-// The fused step: one CTA per TX x TY tile, one thread per tile cell.
+// The fused step: one CTA per TX x TY tile, one thread per tile cell (plus
+// two warps for halo cells and faces).
 //   0. stage the input box (distributions and history, tile + halo) in smem:
-//      one TMA load per array for interior tiles, plain loads with periodic
-//      wrap / wall mirror for tiles touching the domain edge
+//      one TMA load per array; a tile touching the domain edge then reloads
+//      its out-of-domain cells with plain loads (periodic wrap / wall mirror)
 //   1. phi' = sum_i d^f_i on the tile + 2-cell halo
 //   2. cell macros, equilibria, sources and psi-bar-plus (Eq. 29) on the tile
 //      + 1-cell halo (smem records); psi~+ partials of the tile cells stay in
