@@ -44,8 +44,8 @@
 #include <type_traits>
 
 // FP32 arithmetic on pairs of lanes (one packed FFMA2 / FADD2 / FMUL2
-// instruction for two values) in the face reconstruction and the cell
-// pre-step; 0 keeps every FP32 operation scalar.  (Packing the face
+// instruction for two values) in the phi' sums, the face reconstruction and
+// the cell pre-step; 0 keeps every FP32 operation scalar.  (Packing the face
 // distributions of Eq. 28 as well measured slower on GB300: 0.298 vs 0.288 ms
 // per 2048^2 step, more register moves and spills.)
 #ifndef DUGKS_PACKED_F32
@@ -1190,14 +1190,27 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
 
-    // 1. phi' on the halo-(H+1) region
-    for (int t = tid; t < S::N2; t += S::NT) {
-        const int lx = t % S::HX2, ly = t / S::HX2;
-        const Real *p = box + ly * BX + lx + 3 - H;
-        Real s = p[0];
+    // 1. phi' on the halo-(H+1) region; FP32 with the central scheme: two
+    //    neighbouring cells per thread (8-byte aligned pairs, one packed add
+    //    per plane, the same summation order per cell)
+    if constexpr (DUGKS_PACKED_F32 && !S::F64 && (3 - H) % 2 == 0 && S::HX2 % 2 == 0) {
+        for (int t = tid; t < S::N2 / 2; t += S::NT) {
+            const int lx = (t % (S::HX2 / 2)) * 2, ly = t / (S::HX2 / 2);
+            const float *p = reinterpret_cast<const float *>(box) + ly * BX + lx + 3 - H;
+            float2 s = *reinterpret_cast<const float2 *>(p);
 #pragma unroll
-        for (int k = 1; k < 9; k++) s += p[k * BXY];
-        sphi[t] = s;
+            for (int k = 1; k < 9; k++) s = add2(s, *reinterpret_cast<const float2 *>(p + k * BXY));
+            *reinterpret_cast<float2 *>(reinterpret_cast<float *>(sphi) + ly * S::HX2 + lx) = s;
+        }
+    } else {
+        for (int t = tid; t < S::N2; t += S::NT) {
+            const int lx = t % S::HX2, ly = t / S::HX2;
+            const Real *p = box + ly * BX + lx + 3 - H;
+            Real s = p[0];
+#pragma unroll
+            for (int k = 1; k < 9; k++) s += p[k * BXY];
+            sphi[t] = s;
+        }
     }
     __syncthreads();
 
