@@ -642,46 +642,46 @@ __device__ __forceinline__ void recon_face(const Real *__restrict__ rec, int A, 
                                            Real fb[9], Real gb[9]) {
     if constexpr (DUGKS_PACKED_F32 && std::is_same<Real, float>::value) {
         recon_face_f2<COUPLED, XFACE, RS>(rec, A, B, tstride, tmode, h, fb, gb);
-        return;
-    }
-    // value - h xi.slope = (1/2 + h c_n) a + (1/2 - h c_n) b - h c_t s_t
-    const Real cp = Real(0.5) + h, cm = Real(0.5) - h;
-    const Real ht = tmode == 0 ? Real(0.25) * h : Real(0.5) * h;
+    } else {
+        // value - h xi.slope = (1/2 + h c_n) a + (1/2 - h c_n) b - h c_t s_t
+        const Real cp = Real(0.5) + h, cm = Real(0.5) - h;
+        const Real ht = tmode == 0 ? Real(0.25) * h : Real(0.5) * h;
 #pragma unroll
-    for (int G = 0; G < Rec<COUPLED>::NG; G++) {
-        Real a[4], b[4], an[4], as[4], bn[4], bs[4];
-        ld4(rec + A * RS + 4 * G, a);
-        ld4(rec + B * RS + 4 * G, b);
-        const bool tang = group_tangential<COUPLED, XFACE>(G);
-        if (tang) {
-            if (tmode >= 0) {
-                ld4(rec + (A + tstride) * RS + 4 * G, an);
-                ld4(rec + (B + tstride) * RS + 4 * G, bn);
+        for (int G = 0; G < Rec<COUPLED>::NG; G++) {
+            Real a[4], b[4], an[4], as[4], bn[4], bs[4];
+            ld4(rec + A * RS + 4 * G, a);
+            ld4(rec + B * RS + 4 * G, b);
+            const bool tang = group_tangential<COUPLED, XFACE>(G);
+            if (tang) {
+                if (tmode >= 0) {
+                    ld4(rec + (A + tstride) * RS + 4 * G, an);
+                    ld4(rec + (B + tstride) * RS + 4 * G, bn);
+                }
+                if (tmode <= 0) {
+                    ld4(rec + (A - tstride) * RS + 4 * G, as);
+                    ld4(rec + (B - tstride) * RS + 4 * G, bs);
+                }
             }
-            if (tmode <= 0) {
-                ld4(rec + (A - tstride) * RS + 4 * G, as);
-                ld4(rec + (B - tstride) * RS + 4 * G, bs);
-            }
-        }
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int s = 4 * G + j;
-            if (!Rec<COUPLED>::used(s)) continue;
-            const int k = Rec<COUPLED>::dir(s), m = Rec<COUPLED>::model(s);
-            if (m == 1 && k == 0) continue;
-            const int cn = XFACE ? cx(k) : cy(k), ct = XFACE ? cy(k) : cx(k);
-            Real v;
-            if (cn == 0) v = Real(0.5) * (a[j] + b[j]);
-            else if (cn > 0) v = cp * a[j] + cm * b[j];
-            else v = cm * a[j] + cp * b[j];
-            if (ct != 0) {
-                Real T;  // 4 s_t (central) or 2 s_t (one-sided)
-                if (tmode == 0) T = (an[j] + bn[j]) - (as[j] + bs[j]);
-                else if (tmode > 0) T = (an[j] + bn[j]) - (a[j] + b[j]);
-                else T = (a[j] + b[j]) - (as[j] + bs[j]);
-                v = ct > 0 ? v - ht * T : v + ht * T;
+            for (int j = 0; j < 4; j++) {
+                const int s = 4 * G + j;
+                if (!Rec<COUPLED>::used(s)) continue;
+                const int k = Rec<COUPLED>::dir(s), m = Rec<COUPLED>::model(s);
+                if (m == 1 && k == 0) continue;
+                const int cn = XFACE ? cx(k) : cy(k), ct = XFACE ? cy(k) : cx(k);
+                Real v;
+                if (cn == 0) v = Real(0.5) * (a[j] + b[j]);
+                else if (cn > 0) v = cp * a[j] + cm * b[j];
+                else v = cm * a[j] + cp * b[j];
+                if (ct != 0) {
+                    Real T;  // 4 s_t (central) or 2 s_t (one-sided)
+                    if (tmode == 0) T = (an[j] + bn[j]) - (as[j] + bs[j]);
+                    else if (tmode > 0) T = (an[j] + bn[j]) - (a[j] + b[j]);
+                    else T = (a[j] + b[j]) - (as[j] + bs[j]);
+                    v = ct > 0 ? v - ht * T : v + ht * T;
+                }
+                if (m == 0) fb[k] = v; else gb[k] = v;
             }
-            if (m == 0) fb[k] = v; else gb[k] = v;
         }
     }
 }
@@ -693,6 +693,74 @@ __device__ __forceinline__ Real van_leer(Real s1, Real s2) {
     return s1 * s2 > Real(0) ? Real(2) * s1 * s2 * rcp_r(s1 + s2) : Real(0);
 }
 
+// van Leer's limiter on two lanes: the products, sums and scaling packed, the
+// reciprocal and the extremum test per lane (as van_leer does for one).
+__device__ __forceinline__ float2 van_leer2(float2 s1, float2 s2) {
+    const float2 p = mul2(s1, s2), q = add2(s1, s2);
+    const float2 v = mul2(mul2(f2(2.0f), p), f2(rcp_r(q.x), rcp_r(q.y)));
+    return f2(p.x > 0.0f ? v.x : 0.0f, p.y > 0.0f ? v.y : 0.0f);
+}
+
+// FP32 form of recon_face_upwind: the two lanes of each half of a record
+// group in one packed instruction.  A lane crossing the face reads the
+// profile of the cell it leaves (centre, its normal neighbours, its
+// tangential neighbours, chosen per lane at compile time); in the groups of
+// directions along the face both lanes take the mean of both profiles.
+template <bool COUPLED, bool XFACE, int RS>
+__device__ __forceinline__ void recon_face_upwind_f2(const float *__restrict__ rec, int A, int B, int nstride,
+                                                     int tstride, float h, float fb[9], float gb[9]) {
+    auto ld = [&](int c, int G) { return *reinterpret_cast<const float4 *>(rec + c * RS + 4 * G); };
+    auto half = [](const float4 &v, int P) { return P == 0 ? f2(v.x, v.y) : f2(v.z, v.w); };
+#pragma unroll
+    for (int G = 0; G < Rec<COUPLED>::NG; G++) {
+        const bool tang = group_tangential<COUPLED, XFACE>(G);
+        const float4 a = ld(A, G), b = ld(B, G), am = ld(A - nstride, G), bp = ld(B + nstride, G);
+        float4 an = a, as = a, bn = b, bs = b;
+        if (tang) {
+            an = ld(A + tstride, G);
+            as = ld(A - tstride, G);
+            bn = ld(B + tstride, G);
+            bs = ld(B - tstride, G);
+        }
+#pragma unroll
+        for (int P = 0; P < 2; P++) {
+            const int s0 = 4 * G + 2 * P, s1 = s0 + 1;
+            const bool n0 = Rec<COUPLED>::used(s0) && !(Rec<COUPLED>::model(s0) == 1 && Rec<COUPLED>::dir(s0) == 0);
+            const bool n1 = Rec<COUPLED>::used(s1) && !(Rec<COUPLED>::model(s1) == 1 && Rec<COUPLED>::dir(s1) == 0);
+            if (!n0 && !n1) continue;
+            const int k0 = Rec<COUPLED>::dir(s0), k1 = Rec<COUPLED>::dir(s1);
+            const int cn0 = XFACE ? cx(k0) : cy(k0), cn1 = XFACE ? cx(k1) : cy(k1);
+            const int ct0 = XFACE ? cy(k0) : cx(k0), ct1 = XFACE ? cy(k1) : cx(k1);
+            const float2 A2 = half(a, P), B2 = half(b, P);
+            // profile of the cell on side `up` (+1: A, -1: B) of each lane at x_f - xi h
+            auto profile = [&](int up0, int up1, float2 coef) {
+                const float2 c = f2(up0 > 0 ? A2.x : B2.x, up1 > 0 ? A2.y : B2.y);
+                const float2 m = f2(up0 > 0 ? half(am, P).x : A2.x, up1 > 0 ? half(am, P).y : A2.y);
+                const float2 q = f2(up0 > 0 ? B2.x : half(bp, P).x, up1 > 0 ? B2.y : half(bp, P).y);
+                float2 v = fma2(van_leer2(sub2(c, m), sub2(q, c)), coef, c);
+                if (tang && (ct0 != 0 || ct1 != 0)) {
+                    const float2 tn = f2(up0 > 0 ? half(an, P).x : half(bn, P).x, up1 > 0 ? half(an, P).y : half(bn, P).y);
+                    const float2 ts = f2(up0 > 0 ? half(as, P).x : half(bs, P).x, up1 > 0 ? half(as, P).y : half(bs, P).y);
+                    const float2 ht = f2(ct0 > 0 ? -h : (ct0 < 0 ? h : 0.0f), ct1 > 0 ? -h : (ct1 < 0 ? h : 0.0f));
+                    v = fma2(ht, van_leer2(sub2(c, ts), sub2(tn, c)), v);
+                }
+                return v;
+            };
+            float2 V;
+            if (cn0 != 0 && cn1 != 0) {
+                V = profile(cn0, cn1, f2(cn0 > 0 ? 0.5f - h : h - 0.5f, cn1 > 0 ? 0.5f - h : h - 0.5f));
+            } else {   // a lane along the face: both profiles, their mean there
+                const float2 vA = profile(1, 1, f2(cn0 > 0 ? 0.5f - h : 0.5f, cn1 > 0 ? 0.5f - h : 0.5f));
+                const float2 vB = profile(-1, -1, f2(cn0 < 0 ? h - 0.5f : -0.5f, cn1 < 0 ? h - 0.5f : -0.5f));
+                const float2 M = mul2(f2(0.5f), add2(vA, vB));
+                V = f2(cn0 > 0 ? vA.x : (cn0 < 0 ? vB.x : M.x), cn1 > 0 ? vA.y : (cn1 < 0 ? vB.y : M.y));
+            }
+            if (n0) { if (Rec<COUPLED>::model(s0) == 0) fb[k0] = V.x; else gb[k0] = V.x; }
+            if (n1) { if (Rec<COUPLED>::model(s1) == 0) fb[k1] = V.y; else gb[k1] = V.y; }
+        }
+    }
+}
+
 // Upwind reconstruction (R14) at the face between cells A and B (record
 // indices; B = A + nstride along the face normal): each cell carries a linear
 // profile with van Leer slopes along the normal (cells A - nstride .. B +
@@ -702,38 +770,42 @@ __device__ __forceinline__ Real van_leer(Real s1, Real s2) {
 template <typename Real, bool COUPLED, bool XFACE, int RS>
 __device__ __forceinline__ void recon_face_upwind(const Real *__restrict__ rec, int A, int B, int nstride,
                                                   int tstride, Real h, Real fb[9], Real gb[9]) {
+    if constexpr (DUGKS_PACKED_F32 && std::is_same<Real, float>::value) {
+        recon_face_upwind_f2<COUPLED, XFACE, RS>(rec, A, B, nstride, tstride, h, fb, gb);
+    } else {
 #pragma unroll
-    for (int G = 0; G < Rec<COUPLED>::NG; G++) {
-        Real a[4], b[4], am[4], bp[4], an[4], as[4], bn[4], bs[4];
-        ld4(rec + A * RS + 4 * G, a);
-        ld4(rec + B * RS + 4 * G, b);
-        ld4(rec + (A - nstride) * RS + 4 * G, am);
-        ld4(rec + (B + nstride) * RS + 4 * G, bp);
-        if (group_tangential<COUPLED, XFACE>(G)) {
-            ld4(rec + (A + tstride) * RS + 4 * G, an);
-            ld4(rec + (A - tstride) * RS + 4 * G, as);
-            ld4(rec + (B + tstride) * RS + 4 * G, bn);
-            ld4(rec + (B - tstride) * RS + 4 * G, bs);
-        }
+        for (int G = 0; G < Rec<COUPLED>::NG; G++) {
+            Real a[4], b[4], am[4], bp[4], an[4], as[4], bn[4], bs[4];
+            ld4(rec + A * RS + 4 * G, a);
+            ld4(rec + B * RS + 4 * G, b);
+            ld4(rec + (A - nstride) * RS + 4 * G, am);
+            ld4(rec + (B + nstride) * RS + 4 * G, bp);
+            if (group_tangential<COUPLED, XFACE>(G)) {
+                ld4(rec + (A + tstride) * RS + 4 * G, an);
+                ld4(rec + (A - tstride) * RS + 4 * G, as);
+                ld4(rec + (B + tstride) * RS + 4 * G, bn);
+                ld4(rec + (B - tstride) * RS + 4 * G, bs);
+            }
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int s = 4 * G + j;
-            if (!Rec<COUPLED>::used(s)) continue;
-            const int k = Rec<COUPLED>::dir(s), m = Rec<COUPLED>::model(s);
-            if (m == 1 && k == 0) continue;
-            const int cn = XFACE ? cx(k) : cy(k), ct = XFACE ? cy(k) : cx(k);
-            // A's profile at x_f - xi h: normal offset 1/2 - h cn, tangential -h ct; B's: -1/2 - h cn
-            Real vA = Real(0), vB = Real(0);
-            if (cn >= 0) {
-                vA = a[j] + van_leer(a[j] - am[j], b[j] - a[j]) * (cn > 0 ? Real(0.5) - h : Real(0.5));
-                if (ct != 0) vA -= sgnmul(ct, h * van_leer(a[j] - as[j], an[j] - a[j]));
+            for (int j = 0; j < 4; j++) {
+                const int s = 4 * G + j;
+                if (!Rec<COUPLED>::used(s)) continue;
+                const int k = Rec<COUPLED>::dir(s), m = Rec<COUPLED>::model(s);
+                if (m == 1 && k == 0) continue;
+                const int cn = XFACE ? cx(k) : cy(k), ct = XFACE ? cy(k) : cx(k);
+                // A's profile at x_f - xi h: normal offset 1/2 - h cn, tangential -h ct; B's: -1/2 - h cn
+                Real vA = Real(0), vB = Real(0);
+                if (cn >= 0) {
+                    vA = a[j] + van_leer(a[j] - am[j], b[j] - a[j]) * (cn > 0 ? Real(0.5) - h : Real(0.5));
+                    if (ct != 0) vA -= sgnmul(ct, h * van_leer(a[j] - as[j], an[j] - a[j]));
+                }
+                if (cn <= 0) {
+                    vB = b[j] + van_leer(b[j] - a[j], bp[j] - b[j]) * (cn < 0 ? h - Real(0.5) : Real(-0.5));
+                    if (ct != 0) vB -= sgnmul(ct, h * van_leer(b[j] - bs[j], bn[j] - b[j]));
+                }
+                const Real v = cn > 0 ? vA : (cn < 0 ? vB : Real(0.5) * (vA + vB));
+                if (m == 0) fb[k] = v; else gb[k] = v;
             }
-            if (cn <= 0) {
-                vB = b[j] + van_leer(b[j] - a[j], bp[j] - b[j]) * (cn < 0 ? h - Real(0.5) : Real(-0.5));
-                if (ct != 0) vB -= sgnmul(ct, h * van_leer(b[j] - bs[j], bn[j] - b[j]));
-            }
-            const Real v = cn > 0 ? vA : (cn < 0 ? vB : Real(0.5) * (vA + vB));
-            if (m == 0) fb[k] = v; else gb[k] = v;
         }
     }
 }

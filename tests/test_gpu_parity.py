@@ -307,6 +307,23 @@ def test_upwind_allen_cahn_fp64_and_fp32(S):
     assert np.abs(g32["phi"] - ref["phi"]).max() <= 2e-5
 
 
+def test_upwind_coupled_fp32(S):
+    """The FP32-shifted coupled kernel with the upwind reconstruction (the
+    kernel of the bench's upwind leg) against the FP64 oracle, interior and
+    edge tiles, within FP32 round-off after a few steps."""
+    cfg, f = W.random_state(150, 70, seed=29)
+    cfg["recon"] = "upwind"
+    with S.Solver(dict(cfg, precision="fp32", phi_ref=0.5), **f) as s:
+        s.step(6)
+        got = s.macros()
+    o = Oracle(cfg, **f)
+    o.step(6)
+    ref = o.macros()
+    assert np.abs(got["phi"] - ref["phi"]).max() <= 2e-5
+    assert np.abs(got["ux"] - ref["ux"]).max() <= 1e-7
+    assert np.abs(got["p"] - ref["p"]).max() <= 1e-5
+
+
 def test_bounded_wait_times_out_and_context_survives(S):
     """Failure detection without a fault: a kernel waits, with the step
     kernel's wait function and poll limit, on a barrier nothing completes; it
