@@ -37,3 +37,26 @@ def test_band_worker_protocol_in_process():
     assert got[0] == (3, 0.0)
     assert [b for b, _ in got] == [3, 3, 3] and all(dt > 0 for _, dt in got[1:])
     assert res.empty()
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` on the CPU: one JSON line with the
+    benchmark's keys, the oracle as the reference, its own e2e figure."""
+    import json
+    import subprocess
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["unit"] == "MLUPS" and d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["config"]["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
