@@ -56,6 +56,9 @@
  *      the mean of the two cells, and the tangential component the mean of
  *      the two cells (as R3 takes face values of cell quantities); wall faces
  *      keep u = 0.
+ *  R16 Sec. IV.A keeps one kinematic viscosity for the whole field of the
+ *      stationary bubble: tau_g = nu / RT everywhere, which is Eq. 36 (visc
+ *      = 1) with mu_H / mu_L = rho_H / rho_L; the bubble workloads select it.
  *  R14 Upwind reconstruction (recon = 1; Sec. II.B names the upwind scheme
  *      as the alternative to the central one, and Sec. III.A the fix for
  *      its high-Peclet error, without printing it): each of the two cells

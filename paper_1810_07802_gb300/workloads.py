@@ -103,13 +103,16 @@ def smoothed_deformation(L=512, U=0.02, mobility=0.02, width=4.0, cfl=0.5):
 
 
 def stationary_bubble(N=128, R=32.0, width=4.0, rho_ratio=1000.0, nu=0.1, sigma=0.01,
-                      mobility=0.02, cfl=0.5):
-    """Light bubble (phi = 0) in heavy liquid, periodic N x N (Sec. IV.A, Eq. 45)."""
+                      mobility=0.02, cfl=0.5, visc="linear"):
+    """Light bubble (phi = 0) in heavy liquid, periodic N x N (Sec. IV.A, Eq. 45).
+    Sec. IV.A keeps one kinematic viscosity nu for the whole field, so
+    tau_g = nu / RT everywhere: with mu_H = rho_H nu and mu_L = rho_L nu that is
+    the linear rule of Eq. 36 (reading R16), the default here."""
     X, Y = _centres(N, N)
     r = np.hypot(X - N / 2.0, Y - N / 2.0)
     rho_h, rho_l = rho_ratio, 1.0
     cfg = dict(nx=N, ny=N, model="coupled", cfl=cfl, mobility=mobility, width=width,
-               rho_h=rho_h, rho_l=rho_l, mu_h=rho_h * nu, mu_l=rho_l * nu, sigma=sigma)
+               rho_h=rho_h, rho_l=rho_l, mu_h=rho_h * nu, mu_l=rho_l * nu, sigma=sigma, visc=visc)
     return cfg, _fields(_tanh_profile(r - R, width))
 
 
@@ -208,7 +211,8 @@ def serving_trace(n=100, rate=50.0, seed=20181018, precision="fp32", burst=False
                   steps=None):
     """A seeded stream of coupled solve requests shaped like the serving mix:
     layered Poiseuille (mu* = 100, Nx = 4, Ny in {64..512}), stationary bubbles
-    (N in {64..512}, R = N/4, density ratio in {10, 100, 1000}) and spinodal
+    (N in {64..512}, R = N/4, density ratio in {10, 100, 1000}, the paper's
+    bubble width W = 5, with which ratio 1000 is stable) and spinodal
     boxes (N in {128..1024}), with Poisson arrivals of mean `rate` per second
     (all at t = 0 if burst).  Returns (kind, cfg, fields, steps, arrival)
     tuples.  Step budgets per kind: Poiseuille 400, bubble 100, spinodal 200
@@ -223,7 +227,8 @@ def serving_trace(n=100, rate=50.0, seed=20181018, precision="fp32", burst=False
             cfg, f = layered_poiseuille(ny=int(rng.choice([64, 128, 256, 512])), nx=4, mu_ratio=100.0, mu_h=1.0)
         elif kind == "bubble":
             N = int(rng.choice([64, 128, 256, 512]))
-            cfg, f = stationary_bubble(N=N, R=N / 4.0, rho_ratio=float(rng.choice([10.0, 100.0, 1000.0])))
+            cfg, f = stationary_bubble(N=N, R=N / 4.0, width=5.0,
+                                       rho_ratio=float(rng.choice([10.0, 100.0, 1000.0])))
         else:
             N = int(rng.choice([128, 256, 512, 1024]))
             cfg, f = spinodal(N=N, seed=seed + i)

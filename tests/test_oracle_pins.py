@@ -365,6 +365,46 @@ def test_laplace_law():
     assert abs(ratio - paper) < 0.09, ratio
 
 
+def _thermodynamic_pressure(m, sigma, wd):
+    """P = p0 - kappa phi lap phi + kappa |grad phi|^2 / 2 + p with
+    p0 = phi d(eps)/d(phi) - eps, eps = beta phi^2 (phi - 1)^2 (Sec. IV.A, Eq. 3)."""
+    phi = m["phi"]
+    beta, kappa = 12 * sigma / wd, 1.5 * sigma * wd
+    gx, gy, lp = O.grad_lap(phi)
+    eps = beta * phi ** 2 * (phi - 1) ** 2
+    deps = beta * (2 * phi * (phi - 1) ** 2 + 2 * phi ** 2 * (phi - 1))
+    return phi * deps - eps - kappa * phi * lp + 0.5 * kappa * (gx ** 2 + gy ** 2) + m["p"]
+
+
+@pytest.mark.slow
+def test_laplace_law_density_ratio_1000():
+    """Sec. IV.A at density ratio 1000 with the paper's bubble parameters
+    (W = 5, M = 0.1, one kinematic viscosity 0.1 for the whole field: reading
+    R16, the linear rule): the bulk thermodynamic pressure jumps by sigma / R
+    within 0.93-1.02 of it (the paper: ~96.5 %), the spurious velocity stays
+    small and does not grow, and the density on the centre line follows the
+    tanh profile of Eq. 45."""
+    N, R, sigma, wd = 32, 8.0, 0.01, 5.0
+    cfg, fl = W.stationary_bubble(N=N, R=R, rho_ratio=1000.0, sigma=sigma, width=wd, mobility=0.1)
+    assert cfg["visc"] == "linear"
+    o = O.Oracle(cfg, **fl)
+    o.step(3000)
+    m = o.macros()
+    u_3000 = np.hypot(m["ux"], m["uy"]).max()
+    o.step(1000)
+    m = o.macros()
+    u_4000 = np.hypot(m["ux"], m["uy"]).max()
+    P, phi = _thermodynamic_pressure(m, sigma, wd), m["phi"]
+    ratio = (P[phi < 0.01].mean() - P[phi > 0.99].mean()) / (sigma / R)
+    assert 0.93 < ratio < 1.02, ratio
+    assert u_4000 < 1e-5 and u_4000 < 1.2 * u_3000, (u_3000, u_4000)
+    rho = (cfg["rho_h"] - cfg["rho_l"]) * phi[:, N // 2] + cfg["rho_l"]
+    y = np.arange(N) + 0.5
+    r = np.hypot(N // 2 + 0.5 - N / 2.0, y - N / 2.0)
+    rho_a = (cfg["rho_h"] - cfg["rho_l"]) * (0.5 + 0.5 * np.tanh(2 * (r - R) / wd)) + cfg["rho_l"]
+    assert np.abs(rho - rho_a).max() < 0.02 * cfg["rho_h"], np.abs(rho - rho_a).max()
+
+
 # ------------------------------------------- prescribed velocity fields (Sec. III)
 
 def _E(phi, ref):
@@ -595,18 +635,30 @@ def test_tanh_plane_at_rest_is_an_equilibrium():
     """The tanh profile of width W (the equilibrium of the conservative
     Allen-Cahn equation, Sec. II.A) is kept at rest: after 4000 steps the
     profile has moved by less than 1 % at W = 4, the deviation shrinks like
-    (1/W)^2 (second order in the resolution of the interface), the slab stays
-    mirror-symmetric (W = 4) and its phi mass is conserved."""
+    (1/W)^2 (second order in the resolution of the interface), and its phi
+    mass is conserved.  The slab stays mirror-symmetric to round-off at W = 4.
+    At W = 8 the far field is not yet flat to round-off (phi ~ 3e-4 there), so
+    theta = 4 phi (1 - phi) / W ~ 1.5e-4 multiplies a normal n = grad phi /
+    |grad phi| that round-off can turn where grad phi vanishes: the asymmetry
+    may reach that size, but it must stay below it and must not grow."""
     devs = []
     for wd in (4.0, 8.0):
         cfg, f = W.planar_slab(nx=64, ny=3, width=wd, U=0.0, mobility=0.02)
         o = O.Oracle(cfg, **f)
-        o.step(4000)
+        o.step(1000)
+        row = o.macros()["phi"][1]
+        asym_1000 = np.abs(row - row[::-1]).max()
+        o.step(3000)
         phi = o.macros()["phi"]
+        row = phi[1]
+        asym_4000 = np.abs(row - row[::-1]).max()
         devs.append(np.abs(phi - f["phi0"]).max())
-        if wd == 4.0:   # (at W = 8 the slab's centre is a flat region with 0 < phi < 1,
-            row = phi[1]  # where the sharpening term amplifies round-off asymmetries)
-            assert np.abs(row - row[::-1]).max() < 1e-9
+        if wd == 4.0:
+            assert asym_4000 < 1e-9
+        else:
+            theta_far = 4 * row.min() * (1 - row.min()) / wd
+            assert asym_4000 < theta_far, (asym_4000, theta_far)
+            assert asym_4000 < 1.5 * asym_1000 + 1e-12, (asym_1000, asym_4000)
         assert abs(phi.sum() - f["phi0"].sum()) < 1e-9
     assert devs[0] < 1e-2
     assert 3.0 < devs[0] / devs[1] < 5.0, devs
