@@ -48,7 +48,15 @@ typedef enum {
     DUGKS_ERR_CUDA = -3,         /* a CUDA runtime call failed                 */
     DUGKS_ERR_NONFINITE = -4,    /* a step produced NaN or Inf                 */
     DUGKS_ERR_NONPHYSICAL = -5,  /* a step met rho <= 0 or mu <= 0             */
-    DUGKS_ERR_TIMEOUT = -6,      /* reserved for bounded device waits          */
+    DUGKS_ERR_TIMEOUT = -6,      /* a bounded device wait ran out: in a step,
+                                    the wait for a tile's TMA copy.  A CTA
+                                    that gives up leaves its tile of the
+                                    step's output unwritten, so the state
+                                    after that step is undefined (stale cells);
+                                    restore a checkpoint (dugks_set_state)
+                                    before stepping on.  Later CTAs of the
+                                    same and following steps stage with plain
+                                    loads, and the flag stays set           */
     DUGKS_ERR_UNSUPPORTED = -7,  /* valid request this build does not provide  */
     DUGKS_ERR_BOUNDS = -8        /* a bounds-checked build (DUGKS_BOUNDS_CHECK)
                                     met an out-of-range index; the access was
@@ -259,18 +267,23 @@ dugks_status dugks_batch_destroy(dugks_batch b);
  * phi, ux, uy of n doubles (for example dugks_macros output with
  * dst_is_device = 1) and, optionally, snap = [3][n] doubles (phi, ux, uy of an
  * earlier time; NULL if none), and writes four doubles to the device array
- * out: the phi mass sum(phi), the residuals of Eq. 44 for phi and for u
- * against snap (1.0 when snap is NULL), and max |u|.  It is enqueued on
- * cuda_stream (cudaStream_t or NULL) and does not synchronise.
+ * out: the phi mass sum(phi); the relative residuals
+ * sum((phi - snap_phi)^2) / sum(phi^2) and sum(|u - snap_u|^2) / sum(|u|^2)
+ * (the same quantities dugks_reduce returns; 1.0 when snap is NULL); and
+ * max |u|.  It is enqueued on cuda_stream (cudaStream_t or NULL) and does not
+ * synchronise.
  * It allocates nothing: its per-block partial sums live in a fixed device
  * array inside this library (192 KiB, present on every GPU that loads the
  * library until the process exits), which bounds n to
  * DUGKS_STATIC_REDUCE_MAX_CELLS; larger n, n < 1 or a NULL phi/ux/uy/out
  * return DUGKS_ERR_ARG without launching anything.  The first call on each
  * device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.
- * Every call shares the array: calls that can overlap on the GPU (other
- * streams or host threads) race and must be serialised by the caller. */
+ * the device current, and so does the first call in a new context on it
+ * (after cudaDeviceReset, say); a lookup that fails returns DUGKS_ERR_CUDA
+ * and is tried again on the next call.  Make that first call before any
+ * stream capture.  Every call shares the array: calls that can overlap on
+ * the GPU (other streams or host threads) race and must be serialised by the
+ * caller. */
 #define DUGKS_STATIC_REDUCE_MAX_CELLS 16777216
 dugks_status dugks_reduce_fields_static(const double *phi, const double *ux, const double *uy,
                                         const double *snap, int64_t n, double *out, void *cuda_stream);

@@ -18,6 +18,9 @@
 // reads, so nothing has to be cleared between calls; two calls that overlap
 // on the GPU (different streams, or different host threads) share the array
 // and race.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "dugks.h"
@@ -36,9 +39,27 @@ static_assert(DUGKS_STATIC_REDUCE_MAX_CELLS % kCellsPerBlock == 0, "whole blocks
 // One record of kVals partial sums per block: 4096 x 6 doubles = 192 KiB.
 static __device__ __align__(256) double g_partials[kMaxBlocks * kVals];
 
-double *g_scratch_addr[kMaxDevices];   // device address of g_partials, per device
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices];
+// Set-up state per device: the context the address was looked up in and the
+// address itself (null until a lookup has succeeded).
+std::mutex g_scratch_mu;
+CUcontext g_scratch_ctx[kMaxDevices];
+double *g_scratch_addr[kMaxDevices];
+
+// The calling thread's current context, through the runtime's driver entry
+// point (no libcuda link); null if it cannot be had.
+CUcontext current_context() {
+    static PFN_cuCtxGetCurrent_v4000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (PFN_cuCtxGetCurrent_v4000) nullptr;
+        return reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -130,16 +151,29 @@ extern "C" dugks_status dugks_reduce_fields_static(const double *phi, const doub
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return DUGKS_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return DUGKS_ERR_UNSUPPORTED;
-    // Set-up, once per device with that device current: the host name
-    // g_partials is only a stand-in, so fetch the array's device address.
-    std::call_once(g_scratch_once[dev], [dev] {
-        g_scratch_err[dev] = cudaGetSymbolAddress(reinterpret_cast<void **>(&g_scratch_addr[dev]), g_partials);
-    });
-    if (g_scratch_err[dev] != cudaSuccess || !g_scratch_addr[dev]) return DUGKS_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // Set-up, once per device (and per context on it) with the device
+    // current: the host name g_partials is only a stand-in, so fetch the
+    // array's device address.  A failed lookup is not remembered (the next
+    // call tries again); a context created after cudaDeviceReset is a new
+    // context and gets its own lookup.
+    double *scratch = nullptr;
+    {
+        const CUcontext ctx = current_context();
+        if (!ctx) return DUGKS_ERR_CUDA;
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (g_scratch_ctx[dev] != ctx || !g_scratch_addr[dev]) {
+            double *p = nullptr;
+            if (cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_partials) != cudaSuccess || !p)
+                return DUGKS_ERR_CUDA;
+            g_scratch_ctx[dev] = ctx;
+            g_scratch_addr[dev] = p;
+        }
+        scratch = g_scratch_addr[dev];
+    }
     const int nblocks = (int)((n + kCellsPerBlock - 1) / kCellsPerBlock);
-    static_partial_kernel<<<nblocks, kThreads, 0, st>>>(phi, ux, uy, snap, (long long)n, g_scratch_addr[dev]);
-    static_final_kernel<<<1, 32, 0, st>>>(g_scratch_addr[dev], nblocks, snap != nullptr, out);
+    static_partial_kernel<<<nblocks, kThreads, 0, st>>>(phi, ux, uy, snap, (long long)n, scratch);
+    static_final_kernel<<<1, 32, 0, st>>>(scratch, nblocks, snap != nullptr, out);
     e = cudaGetLastError();
     return e == cudaSuccess ? DUGKS_OK : DUGKS_ERR_CUDA;
 }

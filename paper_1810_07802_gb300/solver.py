@@ -198,12 +198,33 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(_dp)
 
 
+def _check_static_args(torch, phi, ux, uy, out, snap):
+    """The kernel reads n doubles of phi, ux, uy (3n of snap) and writes 4 of
+    out on one device: anything else would read or write past a tensor."""
+    named = [("phi", phi), ("ux", ux), ("uy", uy), ("out", out)] + ([("snap", snap)] if snap is not None else [])
+    for name, t in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CUDA float64 tensor" % name)
+        if t.device != phi.device:
+            raise ValueError("%s is on %s, phi on %s" % (name, t.device, phi.device))
+    n = phi.numel()
+    if n < 1 or ux.numel() != n or uy.numel() != n:
+        raise ValueError("phi, ux and uy must have the same number (>= 1) of elements")
+    if snap is not None and snap.numel() != 3 * n:
+        raise ValueError("snap must hold 3 n = %d elements, got %d" % (3 * n, snap.numel()))
+    if out.numel() < 4:
+        raise ValueError("out must hold at least 4 elements")
+
+
 def reduce_fields_static(phi, ux, uy, out, snap=None, stream=None):
     """dugks_reduce_fields_static on CUDA float64 tensors (no allocation in the
     library): phi, ux, uy of n elements, snap of 3n or None, out of 4 elements
     receives (phi mass, residual of phi, residual of u, max |u|)."""
     import torch
 
+    _check_static_args(torch, phi, ux, uy, out, snap)
     n = phi.numel()
     if n > STATIC_REDUCE_MAX_CELLS:
         raise ValueError("dugks_reduce_fields_static takes at most %d cells, got %d" % (STATIC_REDUCE_MAX_CELLS, n))

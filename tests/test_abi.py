@@ -117,3 +117,17 @@ def test_status_strings_cover_every_code(lib):
         text = lib.dugks_status_string(code).decode()
         assert text and text != "unknown status", (code, name)
     assert lib.dugks_status_string(-99).decode() == "unknown status"
+
+
+def test_static_reduce_binding_rejects_host_tensors():
+    """The binding of dugks_reduce_fields_static refuses, before any call into
+    the library, arguments the kernel could not read safely: host tensors,
+    float32 fields and objects that are not tensors."""
+    import torch
+
+    n = 16
+    h = torch.zeros(n, dtype=torch.float64)
+    out = torch.zeros(4, dtype=torch.float64)
+    for args in ((h, h, h, out), (h.float(), h, h, out), (h.numpy(), h, h, out)):
+        with pytest.raises(ValueError):
+            solver.reduce_fields_static(*args)

@@ -227,3 +227,46 @@ def test_server_retires_a_failing_problem(S):
             assert np.array_equal(r.result[k], m0[k]), (q.rid, k)
     s = summary(recs)
     assert s["failed"] == 1 and s["solves"] == 5
+
+
+def test_batch_members_match_the_oracle(S):
+    """Every member of a mixed batch against the FP64 oracle directly (not
+    through the single-problem kernel): two batched steps, a membership change,
+    then 17 steps (one replay of the 16-step graph and one single step).  FP64
+    members within 1e-10 on phi, p, u and the stored distributions; FP32
+    members within the FP32 round-off bounds the single-problem tests use."""
+    import torch
+
+    from oracle.oracle import Oracle
+
+    probs = problems()
+    st = torch.cuda.Stream()
+    solvers = [S.Solver(c, stream=st, **f) for c, f in probs]
+    late = len(probs) - 1
+    with S.Batch(stream=st) as b:
+        for s in solvers[:late]:
+            b.add(s)
+        b.step(2)
+        b.remove(solvers[0])
+        b.add(solvers[late])
+        b.step(17)
+        b.sync()
+    want = [2] + [19] * (late - 1) + [17]
+    for s, (c, f), n in zip(solvers, probs, want):
+        assert s.step_count == n
+        o = Oracle({k: v for k, v in c.items() if k not in ("precision", "phi_ref", "p_ref", "tile_shape")}, **f)
+        o.step(n)
+        ref = o.macros()
+        got = s.macros()
+        what = "%dx%d %s %s" % (c["nx"], c["ny"], c.get("precision", "fp64"), c.get("model", "coupled"))
+        if c.get("precision", "fp64") == "fp64":
+            for k in ("phi", "p", "ux", "uy"):
+                assert np.abs(got[k] - ref[k]).max() <= 1e-10, (what, k)
+            for name, a, r in zip(("f", "g", "phiu"), s.distributions(), o.state()):
+                assert np.abs(a - r).max() <= 1e-10, (what, name)
+        else:
+            assert np.abs(got["phi"] - ref["phi"]).max() <= 2e-5, what
+            assert np.abs(got["ux"] - ref["ux"]).max() <= 1e-7, what
+            assert np.abs(got["uy"] - ref["uy"]).max() <= 1e-7, what
+            assert np.abs(got["p"] - ref["p"]).max() <= 1e-5, what
+        s.close()

@@ -82,3 +82,63 @@ def test_static_reduce_rejects_oversize_and_null(S):
     with pytest.raises(ValueError):
         big = torch.zeros(S.STATIC_REDUCE_MAX_CELLS + 1, dtype=torch.float64, device="cuda")
         S.reduce_fields_static(big, big, big, out)
+
+
+def _numpy_reduce(phi, ux, uy, snap):
+    """The four outputs in FP64 on the host, from their definitions."""
+    u2 = ux * ux + uy * uy
+    out = [phi.sum(), 1.0, 1.0, np.sqrt(u2).max()]
+    if snap is not None:
+        n = phi.size
+        sp, sx, sy = snap[:n], snap[n:2 * n], snap[2 * n:]
+        out[1] = ((phi - sp) ** 2).sum() / (phi ** 2).sum()
+        out[2] = ((ux - sx) ** 2 + (uy - sy) ** 2).sum() / u2.sum()
+    return np.array(out)
+
+
+@pytest.mark.parametrize("n", [300 * 217, 5 * 4096 + 123, 16777216 - 1000, 16777216])
+def test_static_reduce_across_blocks(S, n):
+    """Fields spanning many 4096-cell blocks, ending in a partly filled block
+    (300 x 217 = 15 blocks + 3,660 cells; 5 blocks + 123), and the largest
+    sizes, whose last block is the last record of the scratch array (partly
+    filled, and full at n = DUGKS_STATIC_REDUCE_MAX_CELLS): all four outputs,
+    with and without a snapshot, against an FP64 reduction on the host, on two
+    calls in a row."""
+    import torch
+
+    assert n <= S.STATIC_REDUCE_MAX_CELLS
+    g = torch.Generator(device="cuda").manual_seed(n % 1000003)
+    phi = torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    ux = 1e-3 * (torch.rand(n, dtype=torch.float64, device="cuda", generator=g) - 0.5)
+    uy = 1e-3 * (torch.rand(n, dtype=torch.float64, device="cuda", generator=g) - 0.5)
+    snap = torch.cat([phi + 1e-6 * torch.rand(n, dtype=torch.float64, device="cuda", generator=g),
+                      ux * 0.9, uy * 1.1])
+    h = [t.cpu().numpy() for t in (phi, ux, uy, snap)]
+    for sn, hs in ((None, None), (snap, h[3])):
+        ref = _numpy_reduce(h[0], h[1], h[2], hs)
+        for _ in range(2):
+            got = static_reduce(S, torch, {"phi": phi, "ux": ux, "uy": uy}, sn)
+            np.testing.assert_allclose(got[:3], ref[:3], rtol=1e-11, atol=0.0)
+            assert got[3] == ref[3]
+
+
+def test_static_reduce_rejects_mismatched_tensors(S):
+    """The binding refuses arguments that would make the kernel read or write
+    past a tensor: wrong dtype, a short ux or uy, a snapshot of n instead of
+    3n elements, a 3-element out, or a non-contiguous field."""
+    import torch
+
+    n = 64
+    f = lambda k, dt=torch.float64: torch.zeros(k, dtype=dt, device="cuda")
+    out = f(4)
+    bad = [
+        (f(n, torch.float32), f(n), f(n), out, None),
+        (f(n), f(n - 1), f(n), out, None),
+        (f(n), f(n), f(n + 1), out, None),
+        (f(n), f(n), f(n), out, f(n)),
+        (f(n), f(n), f(n), f(3), None),
+        (torch.zeros(n, 2, dtype=torch.float64, device="cuda")[:, 0], f(n), f(n), out, None),
+    ]
+    for args in bad:
+        with pytest.raises(ValueError):
+            S.reduce_fields_static(*args[:4], snap=args[4])
