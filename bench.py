@@ -139,6 +139,92 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, via ctypes; reads only) every `period` seconds from a thread
+    while the GPU runs, so that even a few milliseconds of timed steps give
+    many samples.  Falls back to ClockSampler (nvidia-smi) if NVML cannot be
+    loaded.  The device is found by the PCI bus id torch reports."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index, period=0.002):
+        import threading
+
+        self.index, self.period = index, period
+        self.fallback = None
+        self.rows = []
+        self.recording = threading.Event()   # set only while timed steps run
+
+    def record(self, on):
+        if on:
+            self.recording.set()
+        else:
+            self.recording.clear()
+
+    def _open(self):
+        import ctypes
+
+        import torch
+
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        bus = getattr(props, "pci_bus_id", None)
+        ok = False
+        if bus is not None:
+            busid = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), bus, getattr(props, "pci_device_id", 0))
+            ok = nv.nvmlDeviceGetHandleByPciBusId_v2(busid.encode(), ctypes.byref(h)) == 0
+        if not ok and nv.nvmlDeviceGetHandleByIndex_v2(int(self.index), ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle")
+        reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        return nv, h, reasons
+
+    def _run(self):
+        import ctypes
+
+        nv, h, reasons = self.nv, self.h, self.reasons_fn
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+        while not self.stop.is_set():
+            if self.recording.is_set() and nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and \
+                    reasons(h, ctypes.byref(rs)) == 0:
+                self.rows.append((clk.value, mx.value, rs.value))
+            time.sleep(self.period)
+
+    def __enter__(self):
+        import threading
+
+        try:
+            self.nv, self.h, self.reasons_fn = self._open()
+        except (OSError, AttributeError):
+            self.fallback = ClockSampler(self.index).__enter__()
+            return self
+        self.stop = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.fallback is not None:
+            return self.fallback.__exit__(*exc)
+        self.stop.set()
+        self.thread.join(5)
+
+    def summary(self):
+        if self.fallback is not None:
+            return dict(self.fallback.summary(), sampler="nvidia-smi -lms 100")
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, "sampler": "nvml"}
+        sm = [r[0] for r in self.rows]
+        reasons = sorted({name for r in self.rows for bit, name in self.REASONS.items() if r[2] & bit})
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm), "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": reasons, "samples": len(self.rows), "sampler": "nvml every %g ms" % (self.period * 1e3)}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -193,6 +279,16 @@ def profiled_warp_instructions():
         return None
 
 
+def algorithmic_fp64_flops_per_cell():
+    """The method's flops per coupled cell update: the distinct operations of
+    one step of the FP64 oracle (oracle/count_flops.py wrote this number)."""
+    try:
+        with open(os.path.join(ROOT, "oracle", "flops_per_cell.json")) as fh:
+            return float(json.load(fh)["coupled"]["distinct_flops_per_cell"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def profiled_fp64_flops_per_cell():
     """Executed FP64 flops per cell update of the FP64 step kernel (ncu: DFMA
     counted twice, DADD and DMUL once)."""
@@ -217,7 +313,14 @@ def time_steps(solver, stream, steps):
     return start.elapsed_time(end) / 1e3
 
 
-def run_gpu_measure(precision, steps, warmup, world, rank, recon="central"):
+REPEATS = 5   # timed windows of K steps each; the reported time is their median
+
+
+def run_gpu_measure(precision, steps, warmup, world, rank, recon="central", repeats=REPEATS, clock=None):
+    """W untimed steps, then `repeats` windows of exactly K steps, each
+    bracketed by a barrier and a synchronize and timed with CUDA events on
+    the solver's stream (the slowest rank's time per window).  Returns the
+    median window time and the per-window times."""
     import torch
     import torch.distributed as dist
 
@@ -231,17 +334,25 @@ def run_gpu_measure(precision, steps, warmup, world, rank, recon="central"):
     s.step(warmup)
     s.sync()
     mass0 = s.reduce()[0]   # FP64 phi mass on the GPU (outside the timed region)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    secs = time_steps(s, stream, steps)
+    windows = []
+    for _ in range(repeats):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clock is not None:
+            clock.record(True)
+        secs = time_steps(s, stream, steps)
+        if clock is not None:
+            clock.record(False)
+        secs, _ = job_time_and_value(secs, 1, world)
+        windows.append(secs)
     s.sync()   # raises if the device status word reports a non-finite or non-physical step
     mass1, resid_phi, resid_u, umax = s.reduce()
-    secs, _ = job_time_and_value(secs, 1, world)
     s.close()
     cfg["_health"] = {"phi_mass_rel_drift": (mass1 - mass0) / mass0, "resid_phi": resid_phi, "resid_u": resid_u,
-                      "umax": umax, "steps": steps}
-    return secs, cfg
+                      "umax": umax, "steps": steps * repeats}
+    cfg["_windows_s"] = windows
+    return statistics.median(windows), cfg
 
 
 def run_e2e(steps, f_host=None):
@@ -450,8 +561,8 @@ def ours(args):
     solver.lib()
     dev_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if world == 1 else local
 
-    with ClockSampler(dev_index) as clk:
-        secs, cfg = run_gpu_measure("fp32", args.steps, args.warmup, world, rank)
+    with NvmlSampler(dev_index) as clk:
+        secs, cfg = run_gpu_measure("fp32", args.steps, args.warmup, world, rank, clock=clk)
     clocks = clk.summary()
     cells = cfg["nx"] * cfg["ny"]
     value = cells * args.steps * world / secs / 1e6   # secs: the slowest rank's
@@ -483,14 +594,16 @@ def ours(args):
                                    "peak_source": "%d SMs x 4 schedulers x %g MHz (sampled SM clock)" % (sms, mhz)}
     if not args.no_fp64:
         k64 = max(3, min(args.steps, 40))
-        with ClockSampler(dev_index) as clk64:
-            secs64, _ = run_gpu_measure("fp64", k64, 3, world, rank)
+        with NvmlSampler(dev_index) as clk64:
+            secs64, _c64 = run_gpu_measure("fp64", k64, 3, world, rank, clock=clk64)
         ach64 = FP64_BYTES_PER_CELL * cells / (secs64 / k64) / 1e9
         extra["fp64"] = {"value": round(cells * k64 / secs64 / 1e6 * world, 1), "unit": "MLUPS", "steps": k64,
                          "ms_per_step": round(secs64 / k64 * 1e3, 4), "hbm_gbs": round(ach64, 1),
                          "hbm_frac": round(ach64 / peak_gbs, 4), "bound": "fp64 alu",
+                         "window_ms": [round(w * 1e3, 4) for w in _c64["_windows_s"]],
                          "clocks": clk64.summary()}
-        fpc = profiled_fp64_flops_per_cell()
+        fpc = algorithmic_fp64_flops_per_cell()
+        executed = profiled_fp64_flops_per_cell()
         if fpc is not None:
             import torch
 
@@ -502,13 +615,18 @@ def ours(args):
             extra["fp64"]["roofline"] = {"bound": "alu", "achieved": round(ach / 1e9, 1),
                                          "peak": round(peak64 / 1e9, 1), "unit": "GFLOP/s",
                                          "frac": round(ach / peak64, 4), "flops_per_cell": fpc,
+                                         "flops_source": "distinct operations of one FP64 oracle step per cell "
+                                                         "(oracle/count_flops.py)",
+                                         "executed_flops_per_cell": executed,
+                                         "executed_over_algorithmic": (round(executed / fpc, 4)
+                                                                       if executed is not None else None),
                                          "peak_source": "%d SMs x 2 DFMA/cycle x 2 flops x %g MHz (sampled SM "
                                                         "clock)" % (sms, mhz)}
     if not args.no_upwind:
         # the upwind reconstruction (van Leer slopes) on the same workload, FP32-shifted
         ku = max(3, min(args.steps, 200))
-        with ClockSampler(dev_index) as clku:
-            secsu, _ = run_gpu_measure("fp32", ku, 3, world, rank, recon="upwind")
+        with NvmlSampler(dev_index) as clku:
+            secsu, _cu = run_gpu_measure("fp32", ku, 3, world, rank, recon="upwind", clock=clku)
         achu = FP32_BYTES_PER_CELL * cells / (secsu / ku) / 1e9
         extra["upwind_fp32"] = {"value": round(cells * ku / secsu / 1e6 * world, 1), "unit": "MLUPS", "steps": ku,
                                 "ms_per_step": round(secsu / ku * 1e3, 5), "hbm_gbs": round(achu, 1),
@@ -522,9 +640,16 @@ def ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64 spinodal field)",
             "config": dict(config_dict("fp32"), parallelism="replicas" if world > 1 else "single GPU"),
             "health": cfg.get("_health"),
+            "timing": {"windows": REPEATS, "steps_per_window": args.steps, "statistic": "median",
+                       "window_ms": [round(w * 1e3, 4) for w in cfg["_windows_s"]],
+                       "ms_x_median_sm_mhz_per_step": (round(ms_step * clocks["sm_mhz"], 1)
+                                                       if clocks.get("sm_mhz") else None)},
             "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps}
     if rank == 0:
         line["e2e"] = run_e2e(args.steps)
+        if args.steps < 400:
+            # the same path at a step count where create and read-back are amortised
+            line["e2e"]["steady_state"] = run_e2e(400)
         if not args.no_serving:
             line["serving"] = run_serving()
         if not args.no_cpu_baseline:

@@ -117,8 +117,10 @@ typedef struct {
     double vel_length;     /* L0 > 0 of velocity fields 1-3                        */
     int32_t recon;         /* dugks_recon: reconstruction of psi-bar-plus at
                               x_f - xi h (Eq. 27): central (default, Sec. II.B) or
-                              upwind with van Leer-limited slopes (periodic y and
-                              the default tile shape only)                         */
+                              upwind with van Leer-limited slopes (the default
+                              tile shape only; with walls a cell next to a wall
+                              takes its one-sided y-difference into the fluid and
+                              the wall face bounces back entering directions)     */
     int32_t reserved3;     /* must be 0                                            */
 } dugks_params;
 

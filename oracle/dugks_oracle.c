@@ -67,7 +67,12 @@
  *      differences, sigma = 2 s1 s2 / (s1 + s2) if s1 s2 > 0 else 0; the
  *      value at x_f - xi h is taken from the profile of the upwind cell
  *      (the one xi . n points away from), and for xi . n = 0 it is the mean
- *      of the two profiles.  Periodic boundaries only.
+ *      of the two profiles.
+ *  R17 The upwind reconstruction with no-slip walls (R9 for the profiles of
+ *      R14): a cell of the first or last row takes its one-sided y-difference
+ *      into the fluid as its y-slope; at a wall face a direction leaving the
+ *      fluid or running along the wall takes the adjacent cell's profile at
+ *      x_f - xi h, one entering the fluid bounces back.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -474,21 +479,33 @@ static double van_leer(double s1, double s2)
     return s1 * s2 > 0.0 ? 2.0 * s1 * s2 / (s1 + s2) : 0.0;
 }
 
-/* R14 at the periodic x-face between columns i and i+1 of row j. */
+/* y-slope of the upwind profile of cell (i, j) (R14): van Leer's limiter of
+ * its two one-sided differences; with walls (R17) a cell of the first or last
+ * row takes its one-sided difference into the fluid instead. */
+static double upwind_yslope(const oracle_params *P, const double *b, int i, int j)
+{
+    int nx = P->nx, ny = P->ny;
+    double c = b[(long)j * nx + i];
+    if (P->wall_y && j == 0) return b[(long)1 * nx + i] - c;
+    if (P->wall_y && j == ny - 1) return c - b[(long)(ny - 2) * nx + i];
+    int jm = (j - 1 + ny) % ny, jp = (j + 1) % ny;
+    return van_leer(c - b[(long)jm * nx + i], b[(long)jp * nx + i] - c);
+}
+
+/* R14 at the x-face between columns i and i+1 of row j (periodic x). */
 static void recon_xface_upwind(const oracle_params *P, const double *B, int i, int j, double *out)
 {
     int nx = P->nx, ny = P->ny;
     long N = (long)nx * ny;
     double h = 0.5 * P->cfl;
     int im = (i - 1 + nx) % nx, ip = (i + 1) % nx, ipp = (i + 2) % nx;
-    int jm = (j - 1 + ny) % ny, jp = (j + 1) % ny;
     for (int q = 0; q < Q; q++) {
         const double *b = B + q * N;
         double L = b[(long)j * nx + i], R = b[(long)j * nx + ip];
         double sxL = van_leer(L - b[(long)j * nx + im], R - L);
         double sxR = van_leer(R - L, b[(long)j * nx + ipp] - R);
-        double syL = van_leer(L - b[(long)jm * nx + i], b[(long)jp * nx + i] - L);
-        double syR = van_leer(R - b[(long)jm * nx + ip], b[(long)jp * nx + ip] - R);
+        double syL = upwind_yslope(P, b, i, j);
+        double syR = upwind_yslope(P, b, ip, j);
         /* x_f - xi h relative to the centre of L is (1/2 - h ex, -h ey), of R (-1/2 - h ex, -h ey) */
         double vL = L + sxL * (0.5 - h * EX[q]) + syL * (-h * EY[q]);
         double vR = R + sxR * (-0.5 - h * EX[q]) + syR * (-h * EY[q]);
@@ -496,19 +513,19 @@ static void recon_xface_upwind(const oracle_params *P, const double *B, int i, i
     }
 }
 
-/* R14 at the periodic y-face between rows jm (below) and jc of column i. */
+/* R14 at the interior (or periodic) y-face between rows jm (below) and jc of
+ * column i. */
 static void recon_yface_upwind(const oracle_params *P, const double *B, int i, int jm, int jc, double *out)
 {
-    int nx = P->nx, ny = P->ny;
-    long N = (long)nx * ny;
+    int nx = P->nx;
+    long N = (long)nx * P->ny;
     double h = 0.5 * P->cfl;
     int im = (i - 1 + nx) % nx, ip = (i + 1) % nx;
-    int jmm = (jm - 1 + ny) % ny, jcp = (jc + 1) % ny;
     for (int q = 0; q < Q; q++) {
         const double *b = B + q * N;
         double D = b[(long)jm * nx + i], U = b[(long)jc * nx + i];
-        double syD = van_leer(D - b[(long)jmm * nx + i], U - D);
-        double syU = van_leer(U - D, b[(long)jcp * nx + i] - U);
+        double syD = upwind_yslope(P, b, i, jm);
+        double syU = upwind_yslope(P, b, i, jc);
         double sxD = van_leer(D - b[(long)jm * nx + im], b[(long)jm * nx + ip] - D);
         double sxU = van_leer(U - b[(long)jc * nx + im], b[(long)jc * nx + ip] - U);
         /* x_f - xi h relative to the centre of D is (-h ex, 1/2 - h ey), of U (-h ex, -1/2 - h ey) */
@@ -554,6 +571,40 @@ static void recon_wall(const oracle_params *P, const double *B, int i, int top, 
         int enters_fluid = top ? (EY[q] < 0) : (EY[q] > 0);
         if (enters_fluid) out[q] = out[opposite(q)];
     }
+}
+
+/* R17 at a wall face of column i with the upwind reconstruction: a direction
+ * leaving the fluid or running along the wall takes the upwind profile of
+ * the adjacent cell (its limited x-slope, its one-sided y-slope into the
+ * fluid) at x_f - xi h; a direction entering the fluid takes the value of
+ * its opposite direction (bounce-back). */
+static void recon_wall_upwind(const oracle_params *P, const double *B, int i, int top, double *out)
+{
+    int nx = P->nx, ny = P->ny;
+    long N = (long)nx * ny;
+    double h = 0.5 * P->cfl;
+    int ip = (i + 1) % nx, im = (i - 1 + nx) % nx;
+    int j0 = top ? ny - 1 : 0;         /* cell adjacent to the wall */
+    double dyw = top ? 0.5 : -0.5;     /* wall position minus cell centre */
+    for (int q = 0; q < Q; q++) {
+        int leaves_fluid_or_tangent = top ? (EY[q] >= 0) : (EY[q] <= 0);
+        if (!leaves_fluid_or_tangent) continue;
+        const double *b = B + q * N;
+        double b0 = b[(long)j0 * nx + i];
+        double sx = van_leer(b0 - b[(long)j0 * nx + im], b[(long)j0 * nx + ip] - b0);
+        double sy = upwind_yslope(P, b, i, j0);
+        out[q] = b0 + (-h * EX[q]) * sx + (dyw - h * EY[q]) * sy;
+    }
+    for (int q = 0; q < Q; q++) {
+        int enters_fluid = top ? (EY[q] < 0) : (EY[q] > 0);
+        if (enters_fluid) out[q] = out[opposite(q)];
+    }
+}
+
+void oracle_wall_face_bar(const oracle_params *P, const double *B, int i, int top, double *out)
+{
+    if (P->recon == 1) recon_wall_upwind(P, B, i, top, out);
+    else recon_wall(P, B, i, top, out);
 }
 
 static void one_step(oracle_ctx *c)
@@ -624,8 +675,13 @@ static void one_step(oracle_ctx *c)
             if (P->wall_y && (j == 0 || j == ny)) {
                 int top = (j == ny);
                 long k0 = (long)(top ? ny - 1 : 0) * nx + i;
-                recon_wall(P, fbp, i, top, fb);
-                if (coupled) recon_wall(P, gbp, i, top, gb);
+                if (P->recon == 1) {
+                    recon_wall_upwind(P, fbp, i, top, fb);
+                    if (coupled) recon_wall_upwind(P, gbp, i, top, gb);
+                } else {
+                    recon_wall(P, fbp, i, top, fb);
+                    if (coupled) recon_wall(P, gbp, i, top, gb);
+                }
                 face_distributions(c, fb, gb, cs[k0].dphix, 0.0, cs[k0].lap, cs[k0].Dx, 0.0,
                                    1, (double)i + 0.5, (double)j, NULL, fp, gp);
             } else {
@@ -685,7 +741,7 @@ static int params_valid(const oracle_params *P)
     if (!(P->cfl > 0.0) || !(P->mobility > 0.0) || !(P->width > 0.0)) return 0;
     if (P->model != 0 && P->model != 1) return 0;
     if (P->velocity_field < 0 || P->velocity_field > 4) return 0;
-    if (P->recon < 0 || P->recon > 1 || (P->recon == 1 && P->wall_y)) return 0;
+    if (P->recon < 0 || P->recon > 1) return 0;
     if (P->model == 1 && P->velocity_field >= 1 && P->velocity_field <= 3 &&
         (!(P->vel_u0 > 0.0) || !(P->vel_length > 0.0))) return 0;
     if (P->model == 0) {

@@ -46,7 +46,7 @@ typedef struct {
     int reserved;
     double vel_u0;       /* U0 of fields 1-3                                   */
     double vel_length;   /* L0 of fields 1-3                                   */
-    int recon;           /* 0 central (R2), 1 upwind with van Leer slopes (R14; periodic y only) */
+    int recon;           /* 0 central (R2), 1 upwind with van Leer slopes (R14; walls: R17) */
     int reserved2;
 } oracle_params;
 
@@ -99,6 +99,10 @@ void oracle_grad_lap(int nx, int ny, int wall_y, const double *phi,
  * the interior or periodic x-face i+1/2 of row j (xface != 0) or the y-face
  * below row j of column i (xface == 0). */
 void oracle_face_bar(const oracle_params *params, const double *B, int i, int j, int xface, double *out);
+/* Face value psi_bar(x_f, t + h) of every direction at the wall face of
+ * column i (walled grids): the bottom wall y = 0 (top == 0) or the top wall
+ * y = ny, by R9 (central) or R17 (upwind). */
+void oracle_wall_face_bar(const oracle_params *params, const double *B, int i, int top, double *out);
 
 #ifdef __cplusplus
 }

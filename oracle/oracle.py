@@ -67,6 +67,7 @@ def lib():
         L.oracle_set_velocity.restype = ctypes.c_int
         L.oracle_set_velocity.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
         L.oracle_face_bar.argtypes = [ctypes.POINTER(OracleParams), _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+        L.oracle_wall_face_bar.argtypes = [ctypes.POINTER(OracleParams), _dp, ctypes.c_int, ctypes.c_int, _dp]
         _lib = L
     return _lib
 
@@ -232,4 +233,13 @@ def face_bar(cfg, B, i, j, xface):
     B = _f64(B, (Q, p.ny, p.nx))
     out = np.zeros(Q)
     lib().oracle_face_bar(ctypes.byref(p), _ptr(B), int(i), int(j), 1 if xface else 0, _ptr(out))
+    return out
+
+
+def wall_face_bar(cfg, B, i, top=False):
+    """psi_bar at the wall face of column i (bottom or top wall) from B [Q][ny][nx]."""
+    p = make_params(cfg)
+    B = _f64(B, (Q, p.ny, p.nx))
+    out = np.zeros(Q)
+    lib().oracle_wall_face_bar(ctypes.byref(p), _ptr(B), int(i), 1 if top else 0, _ptr(out))
     return out

@@ -288,8 +288,7 @@ dugks_status dugks_create(const dugks_params *params, const double *phi0, const 
     *out = nullptr;
     if (!valid(params) || !phi0) return DUGKS_ERR_ARG;
     if (params->bc_x != DUGKS_BC_PERIODIC) return DUGKS_ERR_UNSUPPORTED;
-    if (params->recon == DUGKS_RECON_UPWIND && (params->bc_y != DUGKS_BC_PERIODIC || params->tile_shape > 1))
-        return DUGKS_ERR_UNSUPPORTED;
+    if (params->recon == DUGKS_RECON_UPWIND && params->tile_shape > 1) return DUGKS_ERR_UNSUPPORTED;
     const Layout L = layout(params);
     if (device_workspace && (reinterpret_cast<uintptr_t>(device_workspace) % kAlign)) return DUGKS_ERR_ARG;
     if (device_workspace && ws_bytes < L.total) return DUGKS_ERR_OOM;

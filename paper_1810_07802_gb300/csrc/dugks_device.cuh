@@ -25,9 +25,12 @@
 //     centres at t_n, at face centres at t_n + h, face coordinates on
 //     periodic axes taken in [0, n); or sampled arrays (cells, optional face
 //     normals; otherwise faces take the mean of their two cells).
-//   * Upwind reconstruction (optional, periodic only): each cell of a face
-//     carries a linear profile with van Leer-limited slopes; a direction takes
-//     the profile of the cell it leaves, one along the face the mean of both.
+//   * Upwind reconstruction (optional): each cell of a face carries a linear
+//     profile with van Leer-limited slopes; a direction takes the profile of
+//     the cell it leaves, one along the face the mean of both.  With walls a
+//     cell next to a wall takes its one-sided y-difference into the fluid,
+//     and the wall face takes the adjacent cell's profile for directions
+//     leaving the fluid or running along the wall, bounce-back for the rest.
 //
 // Storage: distributions psi~ as deviations d_i = psi~_i - psi_ref_i from the
 // rest state (f: w_i phi_ref; g: (p_ref/RT)(w_i - delta_i0)), structure of
@@ -708,7 +711,8 @@ __device__ __forceinline__ float2 van_leer2(float2 s1, float2 s2) {
 // directions along the face both lanes take the mean of both profiles.
 template <bool COUPLED, bool XFACE, int RS>
 __device__ __forceinline__ void recon_face_upwind_f2(const float *__restrict__ rec, int A, int B, int nstride,
-                                                     int tstride, float h, float fb[9], float gb[9]) {
+                                                     int tstride, float h, float fb[9], float gb[9], int tmode = 0,
+                                                     bool a_wall = false, bool b_wall = false) {
     auto ld = [&](int c, int G) { return *reinterpret_cast<const float4 *>(rec + c * RS + 4 * G); };
     auto half = [](const float4 &v, int P) { return P == 0 ? f2(v.x, v.y) : f2(v.z, v.w); };
 #pragma unroll
@@ -737,12 +741,20 @@ __device__ __forceinline__ void recon_face_upwind_f2(const float *__restrict__ r
                 const float2 c = f2(up0 > 0 ? A2.x : B2.x, up1 > 0 ? A2.y : B2.y);
                 const float2 m = f2(up0 > 0 ? half(am, P).x : A2.x, up1 > 0 ? half(am, P).y : A2.y);
                 const float2 q = f2(up0 > 0 ? B2.x : half(bp, P).x, up1 > 0 ? B2.y : half(bp, P).y);
-                float2 v = fma2(van_leer2(sub2(c, m), sub2(q, c)), coef, c);
+                float2 sn = van_leer2(sub2(c, m), sub2(q, c));
+                // R17: a cell next to a wall takes its one-sided difference into the fluid
+                if (a_wall || b_wall) {
+                    const float2 one = sub2(B2, A2);
+                    sn = f2((up0 > 0 ? a_wall : b_wall) ? one.x : sn.x, (up1 > 0 ? a_wall : b_wall) ? one.y : sn.y);
+                }
+                float2 v = fma2(sn, coef, c);
                 if (tang && (ct0 != 0 || ct1 != 0)) {
                     const float2 tn = f2(up0 > 0 ? half(an, P).x : half(bn, P).x, up1 > 0 ? half(an, P).y : half(bn, P).y);
                     const float2 ts = f2(up0 > 0 ? half(as, P).x : half(bs, P).x, up1 > 0 ? half(as, P).y : half(bs, P).y);
                     const float2 ht = f2(ct0 > 0 ? -h : (ct0 < 0 ? h : 0.0f), ct1 > 0 ? -h : (ct1 < 0 ? h : 0.0f));
-                    v = fma2(ht, van_leer2(sub2(c, ts), sub2(tn, c)), v);
+                    const float2 st = tmode == 0 ? van_leer2(sub2(c, ts), sub2(tn, c))
+                                                 : (tmode > 0 ? sub2(tn, c) : sub2(c, ts));
+                    v = fma2(ht, st, v);
                 }
                 return v;
             };
@@ -767,11 +779,16 @@ __device__ __forceinline__ void recon_face_upwind_f2(const float *__restrict__ r
 // nstride) and the tangent (A +- tstride, B +- tstride); a direction crossing
 // the face takes the upwind cell's profile at x_f - xi h, one along the face
 // the mean of both.  The rest direction of g is not needed and is skipped.
+// With walls (R17): tmode +1 / -1 takes the one-sided tangential difference
+// towards +t / -t (a cell row next to a wall), and a_wall / b_wall give cell A
+// / B the one-sided normal difference b - a into the fluid (A in the first
+// row above a wall, B in the last row below one).
 template <typename Real, bool COUPLED, bool XFACE, int RS>
 __device__ __forceinline__ void recon_face_upwind(const Real *__restrict__ rec, int A, int B, int nstride,
-                                                  int tstride, Real h, Real fb[9], Real gb[9]) {
+                                                  int tstride, Real h, Real fb[9], Real gb[9], int tmode = 0,
+                                                  bool a_wall = false, bool b_wall = false) {
     if constexpr (DUGKS_PACKED_F32 && std::is_same<Real, float>::value) {
-        recon_face_upwind_f2<COUPLED, XFACE, RS>(rec, A, B, nstride, tstride, h, fb, gb);
+        recon_face_upwind_f2<COUPLED, XFACE, RS>(rec, A, B, nstride, tstride, h, fb, gb, tmode, a_wall, b_wall);
     } else {
 #pragma unroll
         for (int G = 0; G < Rec<COUPLED>::NG; G++) {
@@ -795,13 +812,18 @@ __device__ __forceinline__ void recon_face_upwind(const Real *__restrict__ rec, 
                 const int cn = XFACE ? cx(k) : cy(k), ct = XFACE ? cy(k) : cx(k);
                 // A's profile at x_f - xi h: normal offset 1/2 - h cn, tangential -h ct; B's: -1/2 - h cn
                 Real vA = Real(0), vB = Real(0);
+                auto tslope = [&](Real c, Real sv, Real nv) {
+                    return tmode == 0 ? van_leer(c - sv, nv - c) : (tmode > 0 ? nv - c : c - sv);
+                };
                 if (cn >= 0) {
-                    vA = a[j] + van_leer(a[j] - am[j], b[j] - a[j]) * (cn > 0 ? Real(0.5) - h : Real(0.5));
-                    if (ct != 0) vA -= sgnmul(ct, h * van_leer(a[j] - as[j], an[j] - a[j]));
+                    const Real sA = a_wall ? b[j] - a[j] : van_leer(a[j] - am[j], b[j] - a[j]);
+                    vA = a[j] + sA * (cn > 0 ? Real(0.5) - h : Real(0.5));
+                    if (ct != 0) vA -= sgnmul(ct, h * tslope(a[j], as[j], an[j]));
                 }
                 if (cn <= 0) {
-                    vB = b[j] + van_leer(b[j] - a[j], bp[j] - b[j]) * (cn < 0 ? h - Real(0.5) : Real(-0.5));
-                    if (ct != 0) vB -= sgnmul(ct, h * van_leer(b[j] - bs[j], bn[j] - b[j]));
+                    const Real sB = b_wall ? b[j] - a[j] : van_leer(b[j] - a[j], bp[j] - b[j]);
+                    vB = b[j] + sB * (cn < 0 ? h - Real(0.5) : Real(-0.5));
+                    if (ct != 0) vB -= sgnmul(ct, h * tslope(b[j], bs[j], bn[j]));
                 }
                 const Real v = cn > 0 ? vA : (cn < 0 ? vB : Real(0.5) * (vA + vB));
                 if (m == 0) fb[k] = v; else gb[k] = v;
@@ -813,7 +835,9 @@ __device__ __forceinline__ void recon_face_upwind(const Real *__restrict__ rec, 
 // Wall face, bottom (TOP == false) or top: linear extrapolation from cell c0
 // (next cell into the fluid at c0 + inward) for directions leaving the fluid
 // or tangential, bounce-back for directions entering it.
-template <typename Real, bool COUPLED, bool TOP, int RS>
+// UPW (R17): the tangential slope is van Leer's limited one instead of the
+// central difference.
+template <typename Real, bool COUPLED, bool TOP, int RS, bool UPW = false>
 __device__ __forceinline__ void recon_wall(const Real *__restrict__ rec, int c0, int inward, Real h, Real fb[9],
                                            Real gb[9]) {
     const Real dyw = TOP ? Real(0.5) : Real(-0.5);
@@ -828,7 +852,11 @@ __device__ __forceinline__ void recon_wall(const Real *__restrict__ rec, int c0,
             const Real b0 = rec[c0 * RS + sl];
             const Real sy = TOP ? (b0 - rec[(c0 + inward) * RS + sl]) : (rec[(c0 + inward) * RS + sl] - b0);
             Real v = b0 + (cy(k) == 0 ? dyw : (cy(k) > 0 ? dyw - h : dyw + h)) * sy;
-            if (cx(k) != 0) v -= h * sgnmul(cx(k), Real(0.5) * (rec[(c0 + 1) * RS + sl] - rec[(c0 - 1) * RS + sl]));
+            if (cx(k) != 0) {
+                const Real e = rec[(c0 + 1) * RS + sl], w = rec[(c0 - 1) * RS + sl];
+                const Real sx = UPW ? van_leer(b0 - w, e - b0) : Real(0.5) * (e - w);
+                v -= h * sgnmul(cx(k), sx);
+            }
             out[k] = v;
         }
 #pragma unroll
@@ -1192,7 +1220,6 @@ __device__ __forceinline__ void stage_edges(const StepArgs<Real> &a, int x0, int
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
                                           const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0) {
-    static_assert(!(UPW && WALLY), "the upwind reconstruction is defined for periodic boundaries only");
     using S = TileShape<Real, TX, TY, COUPLED, UPW>;
     constexpr int BXY = S::BXY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1329,13 +1356,12 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
             if (!in_bounds(L - S::HX1 >= 0 && Rr + S::HX1 < S::N1 && (!UPW || (L - 1 >= 0 && Rr + 1 < S::N1)),
                            a.status))
                 continue;
-            if (UPW) {
-                recon_face_upwind<Real, COUPLED, true, RS>(rec, L, Rr, 1, S::HX1, ph.h, fb, gb);
-            } else {
-                int tmode = 0;
-                if (WALLY) tmode = (gyr == 0) ? 1 : ((gyr == ny - 1) ? -1 : 0);
+            int tmode = 0;
+            if (WALLY) tmode = (gyr == 0) ? 1 : ((gyr == ny - 1) ? -1 : 0);
+            if (UPW)
+                recon_face_upwind<Real, COUPLED, true, RS>(rec, L, Rr, 1, S::HX1, ph.h, fb, gb, tmode);
+            else
                 recon_face<Real, COUPLED, true, RS>(rec, L, Rr, S::HX1, tmode, ph.h, fb, gb);
-            }
             ld4(aux + L * AS, au);
             ld4(aux + Rr * AS, bu);
             ady = S::F64 ? aux[L * AS + 4] : sdy[L];
@@ -1370,14 +1396,17 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
                 const int c0 = top ? D : U;
                 if (!in_bounds(c0 - S::HX1 >= 0 && c0 + S::HX1 < S::N1, a.status)) continue;
                 if (top)
-                    recon_wall<Real, COUPLED, true, RS>(rec, c0, -S::HX1, ph.h, fb, gb);
+                    recon_wall<Real, COUPLED, true, RS, UPW>(rec, c0, -S::HX1, ph.h, fb, gb);
                 else
-                    recon_wall<Real, COUPLED, false, RS>(rec, c0, S::HX1, ph.h, fb, gb);
+                    recon_wall<Real, COUPLED, false, RS, UPW>(rec, c0, S::HX1, ph.h, fb, gb);
                 ld4(aux + c0 * AS, au);
                 face_flux<Real, COUPLED, false>(ph, fb, gb, au[0], Real(0), au[2], au[3], Real(0), true, out);
             } else {
-                if (UPW) recon_face_upwind<Real, COUPLED, false, RS>(rec, D, U, S::HX1, 1, ph.h, fb, gb);
-                else recon_face<Real, COUPLED, false, RS>(rec, D, U, 1, 0, ph.h, fb, gb);
+                if (UPW)
+                    recon_face_upwind<Real, COUPLED, false, RS>(rec, D, U, S::HX1, 1, ph.h, fb, gb, 0,
+                                                                WALLY && gyf - 1 == 0, WALLY && gyf == ny - 1);
+                else
+                    recon_face<Real, COUPLED, false, RS>(rec, D, U, 1, 0, ph.h, fb, gb);
                 ld4(aux + D * AS, au);
                 ld4(aux + U * AS, bu);
                 ady = S::F64 ? aux[D * AS + 4] : sdy[D];

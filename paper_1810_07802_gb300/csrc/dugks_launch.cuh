@@ -43,16 +43,16 @@ cudaError_t with_tile(int v, F &&f) {
 
 // Calls f(integral_constant<int, tile>, bool_constant<COUPLED>,
 // bool_constant<WALLY>, bool_constant<UPW>) for the compiled kernel variant.
-// The upwind reconstruction is compiled for the default tile shape and
-// periodic boundaries only.
+// The upwind reconstruction is compiled for the default tile shape only.
 template <typename Real, typename F>
 cudaError_t with_kernel(int tile, bool coupled, bool wally, bool upw, F &&f) {
     using T = std::true_type;
     using U = std::false_type;
     if (upw) {
-        if (tile != 0 || wally) return cudaErrorInvalidValue;
+        if (tile != 0) return cudaErrorInvalidValue;
         const std::integral_constant<int, 0> v0{};
-        return coupled ? f(v0, T{}, U{}, T{}) : f(v0, U{}, U{}, T{});
+        if (coupled) return wally ? f(v0, T{}, T{}, T{}) : f(v0, T{}, U{}, T{});
+        return wally ? f(v0, U{}, T{}, T{}) : f(v0, U{}, U{}, T{});
     }
     return with_tile<Real>(tile, [&](auto v) {
         if (coupled) return wally ? f(v, T{}, T{}, U{}) : f(v, T{}, U{}, U{});

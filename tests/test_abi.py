@@ -95,15 +95,16 @@ def test_tile_shapes_and_their_validation(lib):
 
 
 def test_upwind_limits_rejected_without_gpu(lib):
-    """The upwind reconstruction is compiled for periodic boundaries and the
-    default tile shape: other combinations are refused before any device work."""
+    """The upwind reconstruction is compiled for the default tile shape only:
+    another shape is refused before any device work, as is an unknown
+    reconstruction."""
     import numpy as np
 
     cfg, f = workloads.random_state(16, 12, seed=1)
     phi = np.ascontiguousarray(f["phi0"])
     dp = ctypes.POINTER(ctypes.c_double)
     h = ctypes.c_void_p()
-    for bad in (dict(cfg, recon="upwind", bc_y="wall"), dict(cfg, recon="upwind", tile_shape=2)):
+    for bad in (dict(cfg, recon="upwind", tile_shape=2), dict(cfg, recon="upwind", bc_y="wall", tile_shape=3)):
         p = solver.make_params(bad)
         assert lib.dugks_create(ctypes.byref(p), phi.ctypes.data_as(dp), None, None, None, None, 0, None,
                                 ctypes.byref(h)) == -7

@@ -47,6 +47,8 @@ def problems():
     out.append((dict(cfg, tile_shape=2), f))
     cfg, f = W.random_state(45, 21, seed=4)
     out.append((dict(cfg, recon="upwind"), f))
+    cfg, f = W.random_state(38, 23, seed=6, bc_y="wall")
+    out.append((dict(cfg, recon="upwind", precision="fp32", phi_ref=0.5), f))
     cfg, f = W.zalesak_disk(L=36, R=12.0, slot=3.0, U=0.04)
     r = np.random.default_rng(9)
     out.append((dict(cfg, velocity_field="sampled"),

@@ -44,6 +44,10 @@ cfg, f = W.random_state(37, 29, seed=5)
 errs["upwind 37x29"] = case(dict(cfg, recon="upwind"), f, 4)
 cfg, f = W.random_state(150, 70, seed=6)
 errs["upwind 150x70"] = case(dict(cfg, recon="upwind"), f, 3)
+cfg, f = W.random_state(37, 29, seed=7, bc_y="wall")
+errs["upwind walls 37x29"] = case(dict(cfg, recon="upwind"), f, 4)
+cfg, f = W.random_state(131, 53, seed=8, bc_y="wall")
+errs["upwind walls 131x53"] = case(dict(cfg, recon="upwind"), f, 3)
 cfg, f = W.smoothed_deformation(L=40, U=0.04)
 errs["A-C deformation"] = case(cfg, f, 6)
 for k in range(1, len(S.tile_shapes("fp64")) + 1):

@@ -285,20 +285,24 @@ def test_autotune_picks_a_measured_shape(S):
     assert 1 <= best <= len(ms) and ms[best - 1] == min(ms)
 
 
-@pytest.mark.parametrize("nx,ny,steps", [(150, 70, 6), (37, 29, 9), (5, 7, 3)])
-def test_upwind_reconstruction_fp64(S, nx, ny, steps):
+@pytest.mark.parametrize("nx,ny,steps,bc_y", [(150, 70, 6, "periodic"), (37, 29, 9, "periodic"), (5, 7, 3, "periodic"),
+                                              (150, 70, 6, "wall"), (37, 29, 9, "wall"), (5, 7, 3, "wall"),
+                                              (40, 3, 4, "wall")])
+def test_upwind_reconstruction_fp64(S, nx, ny, steps, bc_y):
     """The upwind reconstruction (van Leer slopes) against the oracle, coupled
     model, with interior (TMA-staged) tiles, ragged tiles and a grid smaller
-    than the halo."""
-    cfg, f = W.random_state(nx, ny, seed=nx * 7 + ny)
+    than the halo; periodic and walled (R17: one-sided slopes next to a wall,
+    the wall face from the adjacent cell's profile), down to three rows."""
+    cfg, f = W.random_state(nx, ny, seed=nx * 7 + ny, bc_y=bc_y)
     cfg["recon"] = "upwind"
     got, ref, dist, st = run_both(S, cfg, f, steps)
     assert_parity(got, ref, dist, st, what="upwind %dx%d" % (nx, ny))
 
 
-def test_upwind_allen_cahn_fp64_and_fp32(S):
+@pytest.mark.parametrize("bc_y", ["periodic", "wall"])
+def test_upwind_allen_cahn_fp64_and_fp32(S, bc_y):
     cfg, f = W.smoothed_deformation(L=64, U=0.04)
-    cfg["recon"] = "upwind"
+    cfg.update(recon="upwind", bc_y=bc_y)
     got, ref, dist, st = run_both(S, cfg, f, 40)
     assert_parity(got, ref, dist, st, what="upwind A-C")
     with S.Solver(dict(cfg, precision="fp32"), **f) as s:
@@ -307,11 +311,12 @@ def test_upwind_allen_cahn_fp64_and_fp32(S):
     assert np.abs(g32["phi"] - ref["phi"]).max() <= 2e-5
 
 
-def test_upwind_coupled_fp32(S):
+@pytest.mark.parametrize("bc_y", ["periodic", "wall"])
+def test_upwind_coupled_fp32(S, bc_y):
     """The FP32-shifted coupled kernel with the upwind reconstruction (the
     kernel of the bench's upwind leg) against the FP64 oracle, interior and
-    edge tiles, within FP32 round-off after a few steps."""
-    cfg, f = W.random_state(150, 70, seed=29)
+    edge tiles, periodic and walled, within FP32 round-off after a few steps."""
+    cfg, f = W.random_state(150, 70, seed=29, bc_y=bc_y)
     cfg["recon"] = "upwind"
     with S.Solver(dict(cfg, precision="fp32", phi_ref=0.5), **f) as s:
         s.step(6)

@@ -209,12 +209,15 @@ def test_initial_state_reproduces_macros():
     np.testing.assert_allclose(m["p"], fl["p0"], atol=1e-15)
 
 
+@pytest.mark.parametrize("recon", ["central", "upwind"])
 @pytest.mark.parametrize("bc_y", ["periodic", "wall"])
-def test_phi_mass_conserved(bc_y):
+def test_phi_mass_conserved(bc_y, recon):
     """Finite-volume fluxes telescope and sum S^f = 0: sum phi is conserved to
-    round-off, with periodic boundaries and with no-slip walls (R9)."""
+    round-off, with periodic boundaries and with no-slip walls (R9; with the
+    upwind reconstruction R17, whose wall face bounces back every entering
+    direction, so no f crosses it)."""
     cfg, fl = W.random_state(19, 17, seed=11, rho_ratio=10.0, bc_y=bc_y)
-    o = O.Oracle(cfg, **fl)
+    o = O.Oracle(dict(cfg, recon=recon), **fl)
     m0 = o.macros()["phi"].sum()
     o.step(60)
     m1 = o.macros()["phi"].sum()
@@ -308,12 +311,14 @@ def test_taylor_green_decay():
     assert amp == pytest.approx(exact, rel=5e-3)
 
 
-def test_single_phase_channel_parabola():
-    """No-slip walls (R9): a body-force channel flow converges to the parabola
-    of Eq. 46 with mu_H = mu_L, to within the wall scheme's second-order error."""
+@pytest.mark.parametrize("recon", ["central", "upwind"])
+def test_single_phase_channel_parabola(recon):
+    """No-slip walls (R9, and R17 for the upwind reconstruction): a body-force
+    channel flow converges to the parabola of Eq. 46 with mu_H = mu_L, to
+    within the wall scheme's second-order error."""
     ny = 32
     cfg, fl = W.layered_poiseuille(ny=ny, mu_ratio=1.0, mu_h=0.1, start_from_analytic=True)
-    o = O.Oracle(cfg, **fl)
+    o = O.Oracle(dict(cfg, recon=recon), **fl)
     o.step(4000)
     u = o.macros()["ux"][:, 0]
     y = np.arange(ny) + 0.5
@@ -547,10 +552,38 @@ def test_upwind_bounded_and_better_at_high_peclet():
     assert res["upwind"][0] < res["central"][0] / 5
 
 
-def test_upwind_rejects_walls():
-    cfg, fl = W.random_state(12, 10, seed=1, bc_y="wall")
-    with pytest.raises(ValueError):
-        O.Oracle(dict(cfg, recon="upwind"), **fl)
+@pytest.mark.parametrize("top", [False, True])
+def test_upwind_wall_face_by_hand(top):
+    """R17 at a wall face, worked by hand on a 6 x 4 walled grid: per direction
+    a ramp in y plus a periodic bump in x.  A direction leaving the fluid or
+    running along the wall takes the adjacent cell's profile at x_f - xi h:
+    its one-sided y-slope into the fluid (the ramp, exactly) and its limited
+    x-slope (column 1 of the bump 0, 1, 3, 1, 0, 0: one-sided differences 1
+    and 2, van Leer 4/3, where the central scheme's wall face would take 3/2);
+    a direction entering the fluid takes its opposite's value.  The central
+    wall face (R9) differs only in that x-slope."""
+    nx, ny, h = 6, 4, 0.25
+    cfg = dict(nx=nx, ny=ny, model="ac", bc_y="wall", cfl=0.5, mobility=0.02, width=4.0, recon="upwind")
+    rng = _rng(31)
+    ex, ey, _ = O.lattice()
+    a, by, cq = rng.standard_normal(9), rng.standard_normal(9), rng.standard_normal(9)
+    bump = np.array([0.0, 1.0, 3.0, 1.0, 0.0, 0.0])
+    Y = (np.arange(ny) + 0.5)[:, None] * np.ones(nx)
+    B = np.stack([a[q] + by[q] * Y + cq[q] * bump[None, :] for q in range(9)])
+    i, j0 = 1, (ny - 1 if top else 0)
+    yw = float(ny) if top else 0.0
+    opp = [0, 5, 6, 7, 8, 1, 2, 3, 4]
+    for recon, sx in (("upwind", 4.0 / 3.0), ("central", 1.5)):
+        want = np.zeros(9)
+        for q in range(9):
+            if (ey[q] >= 0) if top else (ey[q] <= 0):
+                y_at = yw - h * ey[q]                       # x_f - xi h, y component
+                want[q] = (a[q] + by[q] * y_at + cq[q] * bump[i]) + cq[q] * sx * (-h * ex[q])
+        for q in range(9):
+            if (ey[q] < 0) if top else (ey[q] > 0):
+                want[q] = want[opp[q]]
+        got = O.wall_face_bar(dict(cfg, recon=recon), B, i, top=top)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-13, err_msg=recon)
 
 
 # ------------------------------------------------ sampled velocity field (R15)
@@ -662,3 +695,19 @@ def test_tanh_plane_at_rest_is_an_equilibrium():
         assert abs(phi.sum() - f["phi0"].sum()) < 1e-9
     assert devs[0] < 1e-2
     assert 3.0 < devs[0] / devs[1] < 5.0, devs
+
+
+def test_stored_flop_count_is_the_oracles():
+    """The algorithmic flop count the bench's FP64 roofline uses
+    (oracle/flops_per_cell.json) is what counting one oracle step gives now;
+    the distinct count lies below the raw one (the oracle recomputes
+    invariants) and in the 1.5-2.5 kflop range estimated from the scheme's
+    stages (Eqs. 15-19, 27-33) for the coupled model."""
+    from oracle import count_flops
+
+    fresh, saved = count_flops.count(), count_flops.stored()
+    for model in ("coupled", "allen-cahn"):
+        for key in ("flops_per_cell", "distinct_flops_per_cell"):
+            assert fresh[model][key] == pytest.approx(saved[model][key], rel=1e-9), (model, key)
+        assert fresh[model]["distinct_flops_per_cell"] < fresh[model]["flops_per_cell"]
+    assert 1500 < fresh["coupled"]["distinct_flops_per_cell"] < 2500

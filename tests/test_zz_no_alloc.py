@@ -119,7 +119,9 @@ def test_static_reduce_across_blocks(S, n):
         for _ in range(2):
             got = static_reduce(S, torch, {"phi": phi, "ux": ux, "uy": uy}, sn)
             np.testing.assert_allclose(got[:3], ref[:3], rtol=1e-11, atol=0.0)
-            assert got[3] == ref[3]
+            # max |u|: the same cell, its sqrt(ux^2 + uy^2) rounded once more
+            # or less where the device contracts a multiply-add
+            assert got[3] == pytest.approx(ref[3], rel=1e-15)
 
 
 def test_static_reduce_rejects_mismatched_tensors(S):
