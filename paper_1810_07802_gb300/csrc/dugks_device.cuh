@@ -253,7 +253,7 @@ __device__ __forceinline__ void velocity_pressure(Real mx, Real my, Real sn, Rea
     s.uy = (my + half * s.Fy) * s.irho;
     // RT/(1 - w0) = 3/5; rho (Gamma_0(u) - Gamma_0(0)) = -(2/3) rho |u|^2
     s.pd = Real(0.6) * (sn + half * (s.ux * s.drx + s.uy * s.dry)
-                        - Real(2) / Real(3) * s.rho * (s.ux * s.ux + s.uy * s.uy));
+                        - Real(2.0 / 3.0) * s.rho * (s.ux * s.ux + s.uy * s.uy));
 }
 
 // The f model's equilibrium (Eq. 15, as a deviation from w_k phi_ref) and
@@ -894,7 +894,7 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
     s.Dx = Dx;
     s.Dy = Dy;
     closures<Real, COUPLED>(ph, s);
-    if (COUPLED) {
+    if constexpr (COUPLED) {
         Real mx, my, sn;
         moments9(gb, mx, my, sn);
         if (wall) {
@@ -1217,29 +1217,21 @@ __device__ __forceinline__ void stage_edges(const StepArgs<Real> &a, int x0, int
     }
 }
 
+// Phase 0 of a tile: stages the input box [NQ + 2][BY][BX] at `box`, one TMA
+// load per array (an edge tile's out-of-domain cells then overwritten by
+// stage_edges), or plain loads throughout on grids smaller than a tile plus
+// halo.  Ends with the box visible to every thread of the CTA.  Returns false
+// if the CTA gave up on a TMA copy that timed out (STATUS_TIMEOUT is set; the
+// tile must not be computed).
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
-__device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
-                                          const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0) {
+__device__ __forceinline__ bool stage_box(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
+                                          const StepArgs<Real> &a, int x0, int y0, Real *__restrict__ box,
+                                          uint64_t *bar, int *staged_ok) {
     using S = TileShape<Real, TX, TY, COUPLED, UPW>;
     constexpr int BXY = S::BXY;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // 128-byte aligned base for the TMA destinations, whatever the runtime gives
-    Real *sm = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-    Real *box = sm + S::off_box;
-    Real *sphi = sm + S::off_phi;
-    Real *rec = sm + S::off_rec;
-    Real *aux = sm + S::off_aux;
-    Real *sdy = sm + S::off_dy;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S::off_bar);
-    int *staged_ok = reinterpret_cast<int *>(bar + 1);
-
+    constexpr int H = S::H;
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
-
-    // 0. stage the input box [NQ + 2][BY][BX]: one TMA load per array (an
-    //    edge tile's out-of-domain cells then overwritten by stage_edges), or
-    //    plain loads throughout on grids smaller than a tile plus halo
-    constexpr int H = S::H;
     const bool interior = x0 >= 4 && x0 + TX + 4 <= nx && y0 >= H + 1 && y0 + TY + H + 1 <= ny;
     if (tid == 0) {
         int mode = 0;  // 0: plain loads, 1: staged by TMA, 2: TMA timed out
@@ -1259,7 +1251,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     }
     __syncthreads();
     const int mode = *staged_ok;
-    if (mode == 2) return;
+    if (mode == 2) return false;
     if (mode == 1) {
         mbar_wait(bar, 0, 1);  // completed phase: makes the TMA writes visible to this thread
         if (!interior) {
@@ -1270,6 +1262,26 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
         stage_plain<Real, TX, TY, COUPLED, WALLY, UPW>(a, x0, y0, box);
         __syncthreads();
     }
+    return true;
+}
+
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
+__device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
+                                          const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0) {
+    using S = TileShape<Real, TX, TY, COUPLED, UPW>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned base for the TMA destinations, whatever the runtime gives
+    Real *sm = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    Real *box = sm + S::off_box;
+    Real *sphi = sm + S::off_phi;
+    Real *rec = sm + S::off_rec;
+    Real *aux = sm + S::off_aux;
+    Real *sdy = sm + S::off_dy;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S::off_bar);
+    int *staged_ok = reinterpret_cast<int *>(bar + 1);
+
+    // 0. stage the input box [NQ + 2][BY][BX]
+    if (!stage_box<Real, TX, TY, COUPLED, WALLY, UPW>(tm_state_p, tm_hist_p, a, x0, y0, box, bar, staged_ok)) return;
 
     tile_compute<Real, TX, TY, COUPLED, WALLY, UPW>(a, ph, x0, y0, box, sphi, rec, aux, sdy);
 }

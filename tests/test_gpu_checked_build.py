@@ -53,6 +53,19 @@ errs["A-C deformation"] = case(cfg, f, 6)
 for k in range(1, len(S.tile_shapes("fp64")) + 1):
     cfg, f = W.random_state(37, 29, seed=10 + k)
     errs["tile %d" % k] = case(dict(cfg, tile_shape=k), f, 3)
+# FP32 coupled periodic on the default tile shape: checked indices, FP32
+# round-off of the FP64 oracle
+for nx, ny in ((150, 70), (37, 29), (8, 8), (64, 24)):
+    cfg, f = W.random_state(nx, ny, seed=40 + nx)
+    c = dict(cfg, precision="fp32", phi_ref=0.5)
+    with S.Solver(c, **f) as s:
+        s.step(4)
+        got = s.macros()
+    o = Oracle(cfg, **f)
+    o.step(4)
+    ref = o.macros()
+    errs["fp32 %dx%d" % (nx, ny)] = max(float(np.abs(got[k] - ref[k]).max()) / tol
+                                        for k, tol in (("phi", 2e-5), ("ux", 1e-7), ("uy", 1e-7), ("p", 1e-5))) * 1e-10
 print(json.dumps(errs))
 '''
 
