@@ -209,6 +209,26 @@ dugks_status dugks_reduce(dugks_handle h, double *phi_mass, double *resid_phi,
  * Synchronises. */
 dugks_status dugks_get_distributions(dugks_handle h, double *f, double *g, double *phiu_prev);
 
+/* Rows of the state for domain decomposition into y-slabs (no counterpart
+ * in the paper's single-domain runs; the halo a band needs follows from the
+ * stencils of Eqs. 27 and 31-33 and the gradient and Laplacian of Sec. II.B:
+ * two rows of f, one of g and one of (phi u)^{n-1} on each side).
+ * dugks_get_rows copies rows [row0, row0 + nrows) (0 <= row0, row0 + nrows <=
+ * ny) of the current state -- the distribution planes (9 for the
+ * Allen-Cahn-only model, 18 coupled) followed by the 2 history planes,
+ * exactly as stored (FP32 deviations from the rest state, or FP64), in
+ * elements of dugks_state_element_bytes bytes -- into buf laid out
+ * [planes][nrows][nx]; dugks_set_rows copies such a buffer back into those
+ * rows.  buf is device memory (buf_is_device != 0: one kernel on the
+ * solver's stream, no synchronisation) or host memory (synchronises).  Rows
+ * written this way replace the state the next step reads; a band stepped
+ * with its halo rows refreshed from its neighbours before every step gives
+ * its own rows the bits of the single-domain step.  DUGKS_ERR_ARG for rows
+ * outside the grid. */
+size_t dugks_state_element_bytes(dugks_handle h);
+dugks_status dugks_get_rows(dugks_handle h, int32_t row0, int32_t nrows, void *buf, int32_t buf_is_device);
+dugks_status dugks_set_rows(dugks_handle h, int32_t row0, int32_t nrows, const void *buf, int32_t buf_is_device);
+
 /* Checkpoint: size of, and copy of, the complete solver state (header,
  * stored distributions and history exactly as held on the device).
  * Restoring a checkpoint into a handle created with the same parameters

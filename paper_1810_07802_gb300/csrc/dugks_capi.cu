@@ -36,6 +36,38 @@ __global__ void wait_probe_kernel(long max_polls, unsigned *status) {
     }
 }
 
+// Rows [row0, row0 + nrows) of the stored state (nq distribution planes, then
+// the 2 history planes, elements of T) to or from a contiguous buffer
+// [nq + 2][nrows][nx].  One thread per element; the grid covers the buffer.
+template <typename T>
+__global__ void rows_kernel(T *state, T *hist, int nq, int pitch, long long plane, int nx, int row0, int nrows,
+                            T *buf, int to_buf) {
+    const long long n = (long long)(nq + 2) * nrows * nx;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = (int)(i % nx);
+    const long long zr = i / nx;
+    const int r = (int)(zr % nrows), z = (int)(zr / nrows);
+    T *p = z < nq ? state + z * plane : hist + (z - nq) * plane;
+    p += (long long)(row0 + r) * pitch + x;
+    if (to_buf) buf[i] = *p;
+    else *p = buf[i];
+}
+
+cudaError_t launch_rows(void *state, void *hist, size_t elt, int nq, int pitch, long long plane, int nx, int row0,
+                        int nrows, void *buf, int to_buf, cudaStream_t st) {
+    const long long n = (long long)(nq + 2) * nrows * nx;
+    const int bx = 256;
+    const unsigned grid = (unsigned)((n + bx - 1) / bx);
+    if (elt == 4)
+        rows_kernel<float><<<grid, bx, 0, st>>>(static_cast<float *>(state), static_cast<float *>(hist), nq, pitch,
+                                                plane, nx, row0, nrows, static_cast<float *>(buf), to_buf);
+    else
+        rows_kernel<double><<<grid, bx, 0, st>>>(static_cast<double *>(state), static_cast<double *>(hist), nq, pitch,
+                                                 plane, nx, row0, nrows, static_cast<double *>(buf), to_buf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
                           int have_snap, double *partial, double *out, cudaStream_t st) {
     reduce_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(phi, ux, uy, snap, n, have_snap, partial);
@@ -495,6 +527,43 @@ dugks_status dugks_set_state(dugks_handle c, const void *host_buf, size_t bytes)
     c->steps = (int64_t)hd.steps;
     c->have_snap = 0;
     return DUGKS_OK;
+}
+
+size_t dugks_state_element_bytes(dugks_handle c) { return c ? c->L.elt : 0; }
+
+namespace {
+// Rows of the current state to (to_buf) or from a caller buffer: a kernel for
+// device buffers, one 2-D copy per plane for host buffers (then synchronised).
+dugks_status rows_copy(dugks_handle c, int32_t row0, int32_t nrows, void *buf, int32_t buf_is_device, int to_buf) {
+    if (!c || !buf || nrows < 1 || row0 < 0 || row0 + nrows > c->P.ny) return DUGKS_ERR_ARG;
+    const int nq = c->L.nq, nx = c->P.nx;
+    const size_t elt = c->L.elt, row = (size_t)nx * elt, dp = (size_t)c->L.pitch * elt;
+    cudaError_t e = cudaSuccess;
+    if (buf_is_device) {
+        e = dugks::launch_rows(c->state(c->cur), c->hist(c->cur), elt, nq, c->L.pitch, (long long)c->L.plane, nx,
+                               row0, nrows, buf, to_buf, c->st);
+    } else {
+        for (int z = 0; z < nq + 2 && e == cudaSuccess; z++) {
+            unsigned char *plane = static_cast<unsigned char *>(z < nq ? c->state(c->cur) : c->hist(c->cur)) +
+                                   ((size_t)(z < nq ? z : z - nq) * c->L.plane + (size_t)row0 * c->L.pitch) * elt;
+            unsigned char *hb = static_cast<unsigned char *>(buf) + (size_t)z * nrows * row;
+            e = to_buf ? cudaMemcpy2DAsync(hb, row, plane, dp, row, nrows, cudaMemcpyDeviceToHost, c->st)
+                       : cudaMemcpy2DAsync(plane, dp, hb, row, row, nrows, cudaMemcpyHostToDevice, c->st);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    }
+    return from_cuda(e);
+}
+}  // namespace
+
+dugks_status dugks_get_rows(dugks_handle c, int32_t row0, int32_t nrows, void *buf, int32_t buf_is_device) {
+    dugks::TraceRange trace_("dugks_get_rows");
+    return rows_copy(c, row0, nrows, buf, buf_is_device, 1);
+}
+
+dugks_status dugks_set_rows(dugks_handle c, int32_t row0, int32_t nrows, const void *buf, int32_t buf_is_device) {
+    dugks::TraceRange trace_("dugks_set_rows");
+    return rows_copy(c, row0, nrows, const_cast<void *>(buf), buf_is_device, 0);
 }
 
 int64_t dugks_step_count(dugks_handle c) { return c ? c->steps : -1; }

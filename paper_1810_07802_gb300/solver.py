@@ -51,6 +51,11 @@ SIGNATURES = {
     "dugks_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "dugks_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "dugks_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "dugks_state_element_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "dugks_get_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_int32]),
+    "dugks_set_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_int32]),
     "dugks_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -343,6 +348,34 @@ class Solver:
         hh = np.empty((2, self.ny, self.nx))
         _check(lib().dugks_get_distributions(self.h, _ptr(f), _ptr(g), _ptr(hh)), "dugks_get_distributions")
         return f, g, hh
+
+    def row_buffer(self, nrows):
+        """A device tensor shaped [planes][nrows][nx] in the storage precision,
+        for get_rows / set_rows."""
+        import torch
+
+        nq = 18 if self.cfg.get("model", "coupled") == "coupled" else 9
+        dt = torch.float32 if int(lib().dugks_state_element_bytes(self.h)) == 4 else torch.float64
+        return torch.empty((nq + 2, nrows, self.nx), dtype=dt, device=self.device)
+
+    def _rows_arg(self, buf, nrows):
+        import torch
+
+        want = (18 if self.cfg.get("model", "coupled") == "coupled" else 9) + 2
+        esz = int(lib().dugks_state_element_bytes(self.h))
+        if not (isinstance(buf, torch.Tensor) and buf.is_cuda and buf.is_contiguous() and
+                buf.element_size() == esz and buf.numel() == want * nrows * self.nx):
+            raise ValueError("row buffer must be a contiguous CUDA tensor of %d x %d x %d elements of %d bytes"
+                             % (want, nrows, self.nx, esz))
+        return ctypes.c_void_p(buf.data_ptr())
+
+    def get_rows(self, row0, nrows, buf):
+        """Rows [row0, row0 + nrows) of the stored state into buf (see row_buffer); on the solver's stream."""
+        _check(lib().dugks_get_rows(self.h, int(row0), int(nrows), self._rows_arg(buf, nrows), 1), "dugks_get_rows")
+
+    def set_rows(self, row0, nrows, buf):
+        """buf (see row_buffer) into rows [row0, row0 + nrows) of the stored state; on the solver's stream."""
+        _check(lib().dugks_set_rows(self.h, int(row0), int(nrows), self._rows_arg(buf, nrows), 1), "dugks_set_rows")
 
     def get_state(self):
         n = int(lib().dugks_state_bytes(self.h))
