@@ -1,16 +1,27 @@
 """The y-slab decomposition on the GPU: bands of one periodic problem, each a
 Solver on its rows plus two halo rows per side, their halo rows refreshed
 before every step through dugks_get_rows / dugks_set_rows (device buffers,
-exchanged in one process).  Every band's own rows equal the single-domain
-solver's bit for bit, FP64 and FP32-shifted, for two and three bands.  (With
-one GPU per box the same bands over NCCL between GPUs are not run here; the
-exchange protocol on ranks is covered with gloo in test_slab_decomposition.)"""
+exchanged in one process).  (With one GPU per box the same bands over NCCL
+between GPUs are not run here; the exchange protocol on ranks is covered with
+gloo in test_slab_decomposition, bit for bit against the oracle.)
+
+On the GPU a cell's result depends on where the tile grid falls at the
+round-off level: the same problem shifted cyclically by three rows and
+shifted back differs by up to 4.4e-16 (FP64) and one FP32 unit in the last
+place after 7 steps.  A band moves the tile grid the same way, so bands are
+compared with the single-domain solver to round-off, against that shifted
+run as the control, and with the FP64 oracle at the parity bar.  A stale halo
+row changes the band's own rows by about 1e-2 in these random states
+(8.8e-3 measured), far above either bound."""
 import numpy as np
 import pytest
 
 from paper_1810_07802_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+# max |band - single domain| over the stored distributions after 7 steps
+ROUNDOFF = {"fp64": 1e-14, "fp32": 4e-7}
 
 
 @pytest.fixture(scope="module")
@@ -22,7 +33,7 @@ def S():
     return solver
 
 
-@pytest.mark.parametrize("precision,world", [("fp64", 2), ("fp64", 3), ("fp32", 2)])
+@pytest.mark.parametrize("precision,world", [("fp64", 2), ("fp64", 3), ("fp32", 2), ("fp32", 3)])
 def test_bands_equal_the_single_domain(S, precision, world):
     from paper_1810_07802_gb300 import slab
 
@@ -34,16 +45,86 @@ def test_bands_equal_the_single_domain(S, precision, world):
     with S.Solver(cfg, **f) as whole:
         whole.step(steps)
         ref = whole.distributions()
+    shifted = {k: (None if v is None else np.roll(v, 3, axis=0)) for k, v in f.items()}
+    with S.Solver(cfg, **shifted) as s:
+        s.step(steps)
+        control = max(float(np.abs(np.roll(a, -3, axis=1) - b).max()) for a, b in zip(s.distributions(), ref))
     band_list = []
     for r0, r1 in slab.bands(cfg["ny"], world):
+        bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
+        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1))
+    slab.step_bands(slab.LocalExchange(band_list), band_list, steps)
+    worst = 0.0
+    covered = np.zeros(cfg["ny"], dtype=int)
+    for b in band_list:
+        got = b.stepper.distributions()
+        own = slice(slab.HALO, slab.HALO + b.n_own)
+        for g, r in zip(got, ref):
+            worst = max(worst, float(np.abs(g[:, own] - r[:, b.r0:b.r1]).max()))
+        covered[b.r0:b.r1] += 1
+        b.stepper.close()
+    print("\n%s, %d bands: max |band - single domain| %.2e, grid shifted by 3 rows %.2e" % (
+        precision, world, worst, control), end="")
+    assert (covered == 1).all()
+    assert worst <= ROUNDOFF[precision], (worst, control)
+    assert control <= ROUNDOFF[precision], control
+
+
+def test_a_stale_halo_row_is_far_above_the_bound(S):
+    """The bound detects a halo fault: with the outermost halo row of f left
+    stale (zeroed deviations) before each step, the band's own rows move far
+    beyond round-off."""
+    from paper_1810_07802_gb300 import slab
+
+    cfg, f = W.random_state(150, 70, seed=31, rho_ratio=100.0)
+    steps = 7
+    with S.Solver(cfg, **f) as whole:
+        whole.step(steps)
+        ref = whole.distributions()
+    band_list = []
+    for r0, r1 in slab.bands(cfg["ny"], 2):
+        bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
+        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1))
+    exchange = slab.LocalExchange(band_list)
+    b0 = band_list[0]
+    row = b0.stepper.row_buffer(1)
+
+    def faulty():
+        exchange()
+        b0.stepper.get_rows(0, 1, row)
+        row[:9].zero_()
+        b0.stepper.set_rows(0, 1, row)
+
+    slab.step_bands(faulty, band_list, steps)
+    got = b0.stepper.distributions()
+    own = slice(slab.HALO, slab.HALO + b0.n_own)
+    err = max(float(np.abs(g[:, own] - r[:, b0.r0:b0.r1]).max()) for g, r in zip(got, ref))
+    print("\nstale halo row: max |band - single domain| %.2e" % err, end="")
+    for b in band_list:
+        b.stepper.close()
+    assert err > 1e3 * ROUNDOFF["fp64"], err
+
+
+def test_fp64_bands_match_the_oracle(S):
+    """FP64 bands against the single-domain FP64 oracle at the parity bar."""
+    from oracle.oracle import Oracle
+    from paper_1810_07802_gb300 import slab
+
+    cfg, f = W.random_state(150, 70, seed=31, rho_ratio=100.0)
+    steps = 7
+    ref = Oracle(cfg, **f)
+    ref.step(steps)
+    F, G, Hh = ref.state()
+    band_list = []
+    for r0, r1 in slab.bands(cfg["ny"], 3):
         bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
         band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1))
     slab.step_bands(slab.LocalExchange(band_list), band_list, steps)
     for b in band_list:
         got = b.stepper.distributions()
         own = slice(slab.HALO, slab.HALO + b.n_own)
-        for name, g, r in zip(("f", "g", "phiu"), got, ref):
-            assert np.array_equal(g[:, own], r[:, b.r0:b.r1]), (precision, world, b.r0, name)
+        for g, r in zip(got, (F, G, Hh)):
+            assert np.abs(g[:, own] - r[:, b.r0:b.r1]).max() <= 1e-10
         b.stepper.close()
 
 
