@@ -431,6 +431,8 @@ def run_serving(n=100, rate=50.0):
         t_tune += time.perf_counter() - t0
         out[label]["batched_fp32_autotuned"] = keep(summary(BatchingServer(
             budget, max_members=128, chunk=50, keep_results=False, tile_policy=tuner).run(requests("fp32", burst))))
+        out[label]["batched_fp32_persistent"] = keep(summary(BatchingServer(
+            budget, max_members=128, chunk=50, keep_results=False, persistent=True).run(requests("fp32", burst))))
     # accuracy of the FP32 batched results against FP64 solves of the same requests (untimed sample)
     sample32 = requests("fp32", True)[:12]
     sample64 = requests("fp64", True)[:12]

@@ -247,10 +247,18 @@ dugks_status dugks_sync(dugks_handle h);
 dugks_status dugks_destroy(dugks_handle h);
 
 /* ---- Batches: several independent problems advanced together ----
- * A batch advances every member by the same number of DUGKS steps with one
- * launch per kernel variant (precision x model x y-boundary) per step, over a
- * work list of (problem, tile) items, captured once into a CUDA graph and
- * replayed until the membership changes.  Each CTA runs the same tile code as
+ * A batch advances every member by the same number of DUGKS steps.  Members
+ * are grouped by kernel variant (precision x model x y-boundary x tile shape
+ * x reconstruction).  By default each group and step is one grid launch over
+ * the group's (problem, tile) items.  In the persistent mode
+ * (dugks_batch_set_persistent(b, 1)) a group advances up to 16 steps in one
+ * launch: CTAs (at most one step's items, at most as many as fit on the GPU)
+ * take (step, problem, tile) items from one queue in step order, and a tile
+ * of step s + 1 of a member waits only for that member's tiles of step s, so
+ * members of uneven size advance without a batch-wide barrier between steps.
+ * Either way the launches are captured once into CUDA graphs (16 steps, and
+ * one step) and replayed until the membership changes.  The two modes run
+ * separately compiled kernels and agree to round-off.  Each CTA runs the same tile code as
  * dugks_step, with the member's constants read from a device descriptor
  * instead of the kernel's parameter space, so the two agree to round-off.  A
  * member of 2048 tiles or more fills the GPU by itself: it is stepped by
@@ -275,6 +283,13 @@ int32_t dugks_batch_size(dugks_batch b);
 /* Enqueues nsteps >= 0 steps of every member (asynchronous).  The first call
  * after a membership change uploads the work lists and captures the graph. */
 dugks_status dugks_batch_step(dugks_batch b, int64_t nsteps);
+/* Selects the persistent launch (on != 0) or one grid launch per step (on ==
+ * 0, the default) for later dugks_batch_step calls; drops the captured graphs.
+ * A persistent wait that runs out (a fault elsewhere; it does not happen in a
+ * correct run) sets the member's status to DUGKS_ERR_TIMEOUT, reported by
+ * dugks_batch_sync, and leaves that member's state undefined.  Returns
+ * DUGKS_ERR_ARG for a NULL batch. */
+dugks_status dugks_batch_set_persistent(dugks_batch b, int32_t on);
 /* Waits for the batch's stream; returns the first member's error status. */
 dugks_status dugks_batch_sync(dugks_batch b);
 /* Frees the batch (not its members).  Synchronises. */

@@ -3,11 +3,14 @@
 // Members are grouped by kernel variant (precision x model x y-boundary x
 // tile shape x reconstruction).
 // Each group owns a device array of per-problem descriptors (buffers,
-// constants, tensor maps, step counter) and a work list of (problem, tile)
-// items; one batched step is one launch per non-empty group plus a tiny
-// launch that swaps every member's ping-pong buffers.  The launches of one
-// step are captured once into a CUDA graph and replayed until membership
-// changes (one graph of 16 steps and one of a single step).
+// constants, tensor maps, step counter), a work list of (problem, tile)
+// items and 1 + members counters.  By default K steps of a group are one
+// persistent launch (a queue of K x items taken in step order; a tile waits
+// only for its own member's previous step, counted per member) plus a tiny
+// launch that advances every member's buffer parity and step count; the
+// other mode launches one grid per step.  The launches of K steps are
+// captured once into a CUDA graph and replayed until membership changes (one
+// graph of 16 steps and one of a single step).
 //
 // A member of at least kSoloTiles tiles fills the GPU by itself for several
 // waves: it is stepped by the single-problem kernel (as by dugks_step), whose
@@ -47,7 +50,8 @@ struct Group {
     std::vector<int2> h_work;
     void *d_desc = nullptr;
     int2 *d_work = nullptr;
-    size_t desc_cap = 0, work_cap = 0;   // bytes / items allocated
+    unsigned *d_ctr = nullptr;           // queue head + one step counter per member
+    size_t desc_cap = 0, work_cap = 0, ctr_cap = 0;   // bytes / items / counters allocated
     int nwork = 0;
 };
 
@@ -68,6 +72,7 @@ struct dugks_batch_ctx {
     static constexpr int kGroups = 16 * kMaxTiles;
     Group groups[kGroups];   // index: (upw * 8 + fp32 * 4 + coupled * 2 + wally) * kMaxTiles + tile
     bool dirty = true;
+    bool persistent = false;         // K steps per launch (else one grid launch per step)
     // CUDA graphs of one step and of kUnroll steps of the current membership
     static constexpr int kUnroll = 16;
     cudaGraphExec_t exec = nullptr, exec_k = nullptr;
@@ -115,12 +120,13 @@ struct dugks_batch_ctx {
             const size_t ds = desc_size(g.fp32);
             g.h_desc.assign(ds * g.members.size(), 0);
             const int tx = g.fp32 ? dugks::tile_dim<float>(g.tile, 0) : dugks::tile_dim<double>(g.tile, 0);
+            const int ty = g.fp32 ? dugks::tile_dim<float>(g.tile, 1) : dugks::tile_dim<double>(g.tile, 1);
             for (size_t i = 0; i < g.members.size(); i++) {
                 const dugks_ctx *c = g.members[i];
                 if (g.fp32)
-                    fill_desc(reinterpret_cast<InstDesc<float> *>(g.h_desc.data()) + i, c, c->phf, tx);
+                    fill_desc(reinterpret_cast<InstDesc<float> *>(g.h_desc.data()) + i, c, c->phf, tx, ty);
                 else
-                    fill_desc(reinterpret_cast<InstDesc<double> *>(g.h_desc.data()) + i, c, c->phd, tx);
+                    fill_desc(reinterpret_cast<InstDesc<double> *>(g.h_desc.data()) + i, c, c->phd, tx, ty);
             }
             // grow the device arrays (capacity doubling; the graph holds their addresses)
             if (g.h_desc.size() > g.desc_cap) {
@@ -137,6 +143,13 @@ struct dugks_batch_ctx {
                 cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g.d_work), g.work_cap * sizeof(int2));
                 if (e != cudaSuccess) { g.d_work = nullptr; g.work_cap = 0; return e; }
             }
+            if (1 + g.members.size() > g.ctr_cap) {
+                drop_graph();
+                if (g.d_ctr) cudaFree(g.d_ctr);
+                g.ctr_cap = std::max(1 + g.members.size(), 2 * g.ctr_cap);
+                cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g.d_ctr), g.ctr_cap * sizeof(unsigned));
+                if (e != cudaSuccess) { g.d_ctr = nullptr; g.ctr_cap = 0; return e; }
+            }
             cudaError_t e = cudaMemcpyAsync(g.d_desc, g.h_desc.data(), g.h_desc.size(), cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess && dirty)
                 e = cudaMemcpyAsync(g.d_work, g.h_work.data(), g.h_work.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
@@ -147,16 +160,17 @@ struct dugks_batch_ctx {
         return cudaSuccess;
     }
 
-    // One batched step: every non-empty group's launch and buffer swap.
-    cudaError_t enqueue_step() {
+    // k batched steps: every non-empty group's launches and descriptor advances.
+    cudaError_t enqueue_steps(int k) {
         for (Group &g : groups) {
             if (g.members.empty()) continue;
+            unsigned *ctr = persistent ? g.d_ctr : nullptr;
             cudaError_t e = g.fp32 ? dugks::launch_batch_step<float>(g.tile, g.upw, static_cast<InstDesc<float> *>(g.d_desc),
                                                                      g.d_work, g.nwork, (int)g.members.size(),
-                                                                     g.coupled, g.wally, st)
+                                                                     g.coupled, g.wally, k, ctr, st)
                                    : dugks::launch_batch_step<double>(g.tile, g.upw, static_cast<InstDesc<double> *>(g.d_desc),
                                                                       g.d_work, g.nwork, (int)g.members.size(),
-                                                                      g.coupled, g.wally, st);
+                                                                      g.coupled, g.wally, k, ctr, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -173,8 +187,7 @@ struct dugks_batch_ctx {
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        cudaError_t el = cudaSuccess;
-        for (int n = 0; n < steps && el == cudaSuccess; n++) el = enqueue_step();
+        cudaError_t el = enqueue_steps(steps);
         e = cudaStreamEndCapture(st, &graph);
         if (el != cudaSuccess) e = el;
         if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
@@ -242,6 +255,17 @@ dugks_status dugks_batch_step(dugks_batch b, int64_t nsteps) {
     return DUGKS_OK;
 }
 
+dugks_status dugks_batch_set_persistent(dugks_batch b, int32_t on) {
+    if (!b) return DUGKS_ERR_ARG;
+    if (b->persistent != (on != 0)) {
+        cudaError_t e = cudaStreamSynchronize(b->st);   // graphs in flight finish before they are dropped
+        b->persistent = on != 0;
+        b->drop_graph();
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return DUGKS_OK;
+}
+
 dugks_status dugks_batch_sync(dugks_batch b) {
     dugks::TraceRange trace_("dugks_batch_sync");
     if (!b) return DUGKS_ERR_ARG;
@@ -262,6 +286,7 @@ dugks_status dugks_batch_destroy(dugks_batch b) {
     for (Group &g : b->groups) {
         if (g.d_desc) cudaFree(g.d_desc);
         if (g.d_work) cudaFree(g.d_work);
+        if (g.d_ctr) cudaFree(g.d_ctr);
     }
     delete b;
     return from_cuda(e);

@@ -549,6 +549,14 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 #endif
 }
+// Invalidates an initialised barrier whose phases have all completed, so
+// that its memory can be initialised again (a persistent CTA re-arms it for
+// every tile).
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+#ifdef __CUDA_ARCH__
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+#endif
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 #ifdef __CUDA_ARCH__
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -1159,6 +1167,12 @@ __device__ __forceinline__ void tile_compute(const StepArgs<Real> &a, const Phys
                                              Real *__restrict__ box, Real *__restrict__ sphi, Real *__restrict__ rec,
                                              Real *__restrict__ aux, Real *__restrict__ sdy);
 
+// A load of the stored state that bypasses L1 and the read-only path: the
+// persistent batched kernel reads, in a later step of the same launch, state
+// that other CTAs have written, which only L2 holds coherently.
+template <typename Real>
+__device__ __forceinline__ Real ld_state(const Real *p) { return __ldcg(p); }
+
 // Stages the input box [NQ + 2][BY][BX] of the tile at (x0, y0) with plain
 // loads (periodic wrap / wall mirror); no barrier.
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
@@ -1172,7 +1186,8 @@ __device__ __forceinline__ void stage_plain(const StepArgs<Real> &a, int x0, int
         if (!in_bounds(gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny, a.status)) continue;
         const long long g = (long long)gy * a.pitch + gx;
         constexpr int HG = int(S::off_hbox) - S::NQ * BXY;   // alignment gap before the history planes
-        box[(HG != 0 && z >= S::NQ) ? e + HG : e] = z < S::NQ ? a.src[z * a.plane + g] : a.hsrc[(z - S::NQ) * a.plane + g];
+        box[(HG != 0 && z >= S::NQ) ? e + HG : e] = z < S::NQ ? ld_state(a.src + z * a.plane + g)
+                                                               : ld_state(a.hsrc + (z - S::NQ) * a.plane + g);
     }
 }
 
@@ -1213,7 +1228,8 @@ __device__ __forceinline__ void stage_edges(const StepArgs<Real> &a, int x0, int
             continue;
         const long long g = (long long)gy * a.pitch + gx;
         const int b = z * BXY + by * BX + bx;
-        box[(HG != 0 && z >= S::NQ) ? b + HG : b] = z < S::NQ ? a.src[z * a.plane + g] : a.hsrc[(z - S::NQ) * a.plane + g];
+        box[(HG != 0 && z >= S::NQ) ? b + HG : b] = z < S::NQ ? ld_state(a.src + z * a.plane + g)
+                                                               : ld_state(a.hsrc + (z - S::NQ) * a.plane + g);
     }
 }
 
@@ -1226,7 +1242,7 @@ __device__ __forceinline__ void stage_edges(const StepArgs<Real> &a, int x0, int
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 __device__ __forceinline__ bool stage_box(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
                                           const StepArgs<Real> &a, int x0, int y0, Real *__restrict__ box,
-                                          uint64_t *bar, int *staged_ok) {
+                                          uint64_t *bar, int *staged_ok, bool *bar_live = nullptr) {
     using S = TileShape<Real, TX, TY, COUPLED, UPW>;
     constexpr int BXY = S::BXY;
     constexpr int H = S::H;
@@ -1236,6 +1252,10 @@ __device__ __forceinline__ bool stage_box(const CUtensorMap *tm_state_p, const C
     if (tid == 0) {
         int mode = 0;  // 0: plain loads, 1: staged by TMA, 2: TMA timed out
         if (a.use_tma && !a.small && !(*((volatile unsigned *)a.status) & STATUS_TIMEOUT)) {
+            if (bar_live) {   // a CTA that stages several tiles: re-arm the barrier of the last one
+                if (*bar_live) mbar_inval(bar);
+                *bar_live = true;
+            }
             mbar_init(bar, 1);
             mbar_expect_tx(bar, (uint32_t)((S::NQ + 2) * BXY * sizeof(Real)));
             tma_load_3d(box, tm_state_p, x0 - 4, y0 - H - 1, 0, bar);
@@ -1267,7 +1287,8 @@ __device__ __forceinline__ bool stage_box(const CUtensorMap *tm_state_p, const C
 
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const CUtensorMap *tm_hist_p,
-                                          const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0) {
+                                          const StepArgs<Real> &a, const Phys<Real> &ph, int x0, int y0,
+                                          bool *bar_live = nullptr) {
     using S = TileShape<Real, TX, TY, COUPLED, UPW>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 128-byte aligned base for the TMA destinations, whatever the runtime gives
@@ -1281,7 +1302,9 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_state_p, const C
     int *staged_ok = reinterpret_cast<int *>(bar + 1);
 
     // 0. stage the input box [NQ + 2][BY][BX]
-    if (!stage_box<Real, TX, TY, COUPLED, WALLY, UPW>(tm_state_p, tm_hist_p, a, x0, y0, box, bar, staged_ok)) return;
+    if (!stage_box<Real, TX, TY, COUPLED, WALLY, UPW>(tm_state_p, tm_hist_p, a, x0, y0, box, bar, staged_ok,
+                                                       bar_live))
+        return;
 
     tile_compute<Real, TX, TY, COUPLED, WALLY, UPW>(a, ph, x0, y0, box, sphi, rec, aux, sdy);
 }
@@ -1493,6 +1516,7 @@ struct InstDesc {
     long long plane;
     long long steps;                       // step count (batched use)
     int nx, ny, pitch, tiles_x;
+    int ntiles;                            // tiles of one step of this problem
     int cur;                               // buffer holding psi~^n (batched use)
     int use_tma;
     const Real *vel;                       // sampled velocity field, or null
@@ -1547,13 +1571,130 @@ solo_step_kernel(const __grid_constant__ CUtensorMap tm_state, const __grid_cons
                                                  (tile / tiles_x) * TY);
 }
 
-// After a batched step: every instance's buffers swap and its step count grows.
+// K steps of a batch group in one persistent launch.  The CTAs (as many as
+// fit on the GPU) take items from one queue, in order: the items of step 0
+// of every member, then those of step 1, and so on; item i is step i / nwork
+// of the (problem, tile) pair work[i % nwork].  A tile of step s + 1 of a
+// problem waits only until every tile of step s of that problem is done
+// (its counter, ctr[1 + problem], has reached (s + 1) x its tile count), so
+// a small member runs ahead of a large one instead of waiting at a step
+// boundary of the whole batch.  Progress does not depend on the CTAs being
+// resident together: an item is taken only by a running CTA that has
+// finished its previous one, and every item it waits for comes earlier in the
+// queue, so the earliest unfinished item is being worked on and never waits.
+// (Claiming the next item while computing the current one made a CTA hold
+// two items of consecutive steps, which serialised them: FP64 steps of two
+// 128^2 members took 136 us instead of 97.)  Each
+// wait is bounded (about 2 s of sleeps): on running out it flags the problem's
+// status word (STATUS_TIMEOUT) and goes on, so a fault cannot hang the
+// launch.  The counters start at zero (the launcher clears them); the
+// descriptors' buffer parity and step count advance after the launch.
+constexpr unsigned long long kItemWaitNs = 2000000000ull;   // sleep budget of one wait (about 2 s)
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v = 0;
+#ifdef __CUDA_ARCH__
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+#endif
+    return v;
+}
+// Adds 1 with release semantics at GPU scope: the CTA's writes that a barrier
+// ordered before this are visible to whoever acquires the new count.
+__device__ __forceinline__ void red_release_gpu_add1(unsigned *p) {
+#ifdef __CUDA_ARCH__
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+#endif
+}
+// Orders this thread's earlier (generic) observations before its later TMA
+// (async proxy) reads of global memory.
+__device__ __forceinline__ void fence_proxy_async_global() {
+#ifdef __CUDA_ARCH__
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+#endif
+}
+
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW = false>
+__global__ void __launch_bounds__((TileShape<Real, TX, TY, COUPLED, UPW>::NT),
+                                  (TileShape<Real, TX, TY, COUPLED, UPW>::MINB))
+persistent_step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__restrict__ work, int nwork,
+                       int ksteps, unsigned *ctr) {
+    using S = TileShape<Real, TX, TY, COUPLED, UPW>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Real *sm = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    // the queue position, in the spare word after the barrier and the staging flag
+    volatile int *slot = reinterpret_cast<int *>(reinterpret_cast<uint64_t *>(sm + S::off_bar) + 1) + 1;
+    const int tid = threadIdx.x;
+    const unsigned total = (unsigned)ksteps * (unsigned)nwork;
+    bool bar_live = false;
+    if (tid == 0) *slot = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    for (;;) {
+        const unsigned i = (unsigned)*slot;
+        if (i >= total) break;
+        const unsigned s = i / (unsigned)nwork;
+        const int2 item = work[i - s * (unsigned)nwork];
+        const InstDesc<Real> *d = descs + item.x;
+        if (tid == 0) {
+            const unsigned *done = ctr + 1 + item.x;
+            if (s > 0) {
+                const unsigned nt = (unsigned)d->ntiles, need = s * nt;
+                unsigned long long slept = 0;
+                for (unsigned have; (have = ld_acquire_gpu(done)) < need;) {
+                    if (slept > kItemWaitNs) {
+                        atomicOr(d->status, STATUS_TIMEOUT);
+                        break;
+                    }
+                    // back off by the member's distance in steps, so that CTAs
+                    // waiting many steps ahead do not crowd the counter
+                    const unsigned behind = (need - have + nt - 1) / nt;
+                    const unsigned ns = behind > 1 ? (behind < 16 ? 1000u * (behind - 1) : 15000u) : 100u;
+                    __nanosleep(ns);
+                    slept += ns;
+                }
+            }
+            fence_proxy_async_global();
+        }
+        __syncthreads();
+        const int cur = d->cur ^ (int)(s & 1u);
+        const long long steps = d->steps + (long long)s;
+        StepArgs<Real> a;
+        a.src = d->state[cur];
+        a.dst = d->state[cur ^ 1];
+        a.hsrc = d->hist[cur];
+        a.hdst = d->hist[cur ^ 1];
+        a.nx = d->nx;
+        a.ny = d->ny;
+        a.pitch = d->pitch;
+        a.plane = d->plane;
+        a.first_step = steps == 0;
+        a.t_n = double(steps) * double(d->ph.dt);
+        a.small = (a.nx < TX + 4 || a.ny < TY + 4) ? 1 : 0;
+        a.use_tma = d->use_tma;
+        a.vel = d->vel;
+        a.vel_faces = d->vel_faces;
+        a.status = d->status;
+        const Phys<Real> &ph = d->ph;
+        const int tx = item.y % d->tiles_x, ty = item.y / d->tiles_x;
+        step_tile<Real, TX, TY, COUPLED, WALLY, UPW>(&d->tm_state[cur], &d->tm_hist[cur], a, ph, tx * TX, ty * TY,
+                                                     &bar_live);
+        __syncthreads();   // every store of the tile is issued before the release below
+        if (tid == 0) {
+            // the member is looked up again rather than kept in registers through the tile
+            const unsigned j = (unsigned)*slot;
+            red_release_gpu_add1(ctr + 1 + work[j % (unsigned)nwork].x);
+            *slot = (int)atomicAdd(ctr, 1u);
+        }
+        __syncthreads();   // the next position is visible; the tile's shared memory is free
+    }
+}
+
+// After k batched steps: every instance's buffers swap k times and its step count grows by k.
 template <typename Real>
-__global__ void advance_kernel(InstDesc<Real> *descs, int n) {
+__global__ void advance_kernel(InstDesc<Real> *descs, int n, int k) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        descs[i].cur ^= 1;
-        descs[i].steps += 1;
+        descs[i].cur ^= (k & 1);
+        descs[i].steps += k;
     }
 }
 

@@ -39,7 +39,7 @@ template <typename Real>
 cudaError_t batch_prepare(int tile, bool coupled, bool wally, bool upw);
 template <typename Real>
 cudaError_t launch_batch_step(int tile, bool upw, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst,
-                              bool coupled, bool wally, cudaStream_t st);
+                              bool coupled, bool wally, int ksteps, unsigned *ctr, cudaStream_t st);
 cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
                           int have_snap, double *partial, double *out, cudaStream_t st);
 
@@ -131,7 +131,7 @@ cudaError_t step_on(dugks_ctx *c, long long nsteps, cudaStream_t st);
 
 // Descriptor of one problem for the step kernel (device image built on the host).
 template <typename Real>
-inline void fill_desc(InstDesc<Real> *d, const dugks_ctx *c, const Phys<Real> &ph, int tx) {
+inline void fill_desc(InstDesc<Real> *d, const dugks_ctx *c, const Phys<Real> &ph, int tx, int ty) {
     std::memset(static_cast<void *>(d), 0, sizeof *d);
     for (int b = 0; b < 2; b++) {
         d->tm_state[b] = c->tm_state[b];
@@ -147,6 +147,7 @@ inline void fill_desc(InstDesc<Real> *d, const dugks_ctx *c, const Phys<Real> &p
     d->ny = c->P.ny;
     d->pitch = c->L.pitch;
     d->tiles_x = (c->P.nx + tx - 1) / tx;
+    d->ntiles = d->tiles_x * ((c->P.ny + ty - 1) / ty);
     d->cur = c->cur;
     d->use_tma = c->tma_ok ? 1 : 0;
     d->vel = static_cast<const Real *>(c->vel());

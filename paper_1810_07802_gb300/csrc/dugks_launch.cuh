@@ -60,8 +60,16 @@ cudaError_t with_kernel(int tile, bool coupled, bool wally, bool upw, F &&f) {
     });
 }
 
+// CTAs of the persistent batched kernel that fit on the device at once
+// (resident per SM x SMs), per device; set with the kernel attributes below.
+template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
+static int &persistent_capacity(int dev) {
+    static int cap[64];
+    return cap[dev];
+}
+
 // Raises the step kernels' dynamic shared-memory limit, once per device (the
-// attribute belongs to the device's context).
+// attribute belongs to the device's context), and sizes the persistent grid.
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW>
 static cudaError_t step_attr_t() {
     using S = TileShape<Real, TX, TY, COUPLED, UPW>;
@@ -77,7 +85,15 @@ static cudaError_t step_attr_t() {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
         cudaError_t b = cudaFuncSetAttribute(solo_step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
-        result[dev] = a != cudaSuccess ? a : b;
+        cudaError_t c = cudaFuncSetAttribute(persistent_step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
+        int per_sm = 0, sms = 0;
+        if (c == cudaSuccess)
+            c = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_step_kernel<Real, TX, TY, COUPLED, WALLY, UPW>,
+                                                              S::NT, S::smem_bytes);
+        if (c == cudaSuccess) c = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        persistent_capacity<Real, TX, TY, COUPLED, WALLY, UPW>(dev) = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        result[dev] = a != cudaSuccess ? a : (b != cudaSuccess ? b : c);
     });
     return result[dev];
 }
@@ -135,18 +151,46 @@ cudaError_t batch_prepare(int tile, bool coupled, bool wally, bool upw) {
     return step_prepare<Real>(tile, coupled, wally, upw);
 }
 
+// ksteps batched steps of one group.  With ctr (1 + ninst counters): one
+// persistent launch over all ksteps (counters cleared first), then one
+// advance of the descriptors.  Without: ksteps grid launches of one step,
+// each followed by an advance.
 template <typename Real>
 cudaError_t launch_batch_step(int tile, bool upw, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst,
-                              bool coupled, bool wally, cudaStream_t st) {
-    if (nwork <= 0) return cudaSuccess;
-    cudaError_t e = with_kernel<Real>(tile, coupled, wally, upw, [&](auto v, auto c, auto w, auto u) {
-        DUGKS_KERNEL_PARAMS(v, c, w, u)
-        step_kernel<Real, TX, TY, C, W, UP><<<nwork, S::NT, S::smem_bytes, st>>>(descs, work);
-        return cudaGetLastError();
-    });
+                              bool coupled, bool wally, int ksteps, unsigned *ctr, cudaStream_t st) {
+    if (nwork <= 0 || ksteps <= 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    advance_kernel<Real><<<(ninst + 127) / 128, 128, 0, st>>>(descs, ninst);
-    return cudaGetLastError();
+    if (ctr) {
+        e = cudaMemsetAsync(ctr, 0, (size_t)(1 + ninst) * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        e = with_kernel<Real>(tile, coupled, wally, upw, [&](auto v, auto c, auto w, auto u) {
+            DUGKS_KERNEL_PARAMS(v, c, w, u)
+            // at most one step's items: more CTAs would only wait for the next step
+            const int resident = persistent_capacity<Real, TX, TY, C, W, UP>(dev);
+            const int cap = nwork < resident ? nwork : resident;
+            const int grid = cap > 0 ? cap : 1;
+            persistent_step_kernel<Real, TX, TY, C, W, UP><<<grid, S::NT, S::smem_bytes, st>>>(descs, work, nwork,
+                                                                                              ksteps, ctr);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+        advance_kernel<Real><<<(ninst + 127) / 128, 128, 0, st>>>(descs, ninst, ksteps);
+        return cudaGetLastError();
+    }
+    for (int k = 0; k < ksteps; k++) {
+        e = with_kernel<Real>(tile, coupled, wally, upw, [&](auto v, auto c, auto w, auto u) {
+            DUGKS_KERNEL_PARAMS(v, c, w, u)
+            step_kernel<Real, TX, TY, C, W, UP><<<nwork, S::NT, S::smem_bytes, st>>>(descs, work);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+        advance_kernel<Real><<<(ninst + 127) / 128, 128, 0, st>>>(descs, ninst, 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 static inline dim3 cell_grid(int nx, int ny, int bx) { return dim3((nx + bx - 1) / bx, ny); }
@@ -204,6 +248,6 @@ cudaError_t launch_export(const FieldArgs<Real> &a, int nq, double phi_ref, doub
                                              cudaStream_t);                                                        \
     template cudaError_t batch_prepare<Real>(int, bool, bool, bool);                                               \
     template cudaError_t launch_batch_step<Real>(int, bool, InstDesc<Real> *, const int2 *, int, int, bool, bool,  \
-                                                 cudaStream_t);
+                                                 int, unsigned *, cudaStream_t);
 
 }  // namespace dugks

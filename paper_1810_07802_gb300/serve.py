@@ -99,11 +99,13 @@ class BatchingServer:
     chunk: steps enqueued between scheduling decisions at most.
     tile_policy: None (the library's default tile shape) or a callable
       (cfg, fields) -> tile_shape, e.g. an AutotuneCache.
+    persistent: advance the batch in persistent launches of up to 16 steps
+      (dugks_batch_set_persistent) instead of one grid launch per step.
     """
 
     def __init__(self, hbm_budget, max_members=128, chunk=50, stream=None, solver_factory=None,
                  batch_factory=None, footprint=None, clock=time.perf_counter, sleep=time.sleep,
-                 keep_results=True, tile_policy=None):
+                 keep_results=True, tile_policy=None, persistent=False):
         if solver_factory is None:
             import torch
 
@@ -114,7 +116,7 @@ class BatchingServer:
             self.create_stream = stream if stream is not None else torch.cuda.Stream()
             self.batch_stream = torch.cuda.Stream()
             solver_factory = lambda req: S.Solver(req.cfg, stream=self.create_stream, **req.fields)  # noqa: E731
-            batch_factory = batch_factory or (lambda: S.Batch(stream=self.batch_stream))
+            batch_factory = batch_factory or (lambda: S.Batch(stream=self.batch_stream, persistent=persistent))
             footprint = footprint or S.workspace_bytes
         self.hbm_budget = int(hbm_budget)
         self.max_members = int(max_members)

@@ -66,6 +66,7 @@ SIGNATURES = {
     "dugks_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
     "dugks_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "dugks_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "dugks_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "dugks_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_check_bounded_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
     "dugks_set_velocity_field": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
@@ -389,9 +390,11 @@ class Solver:
 
 
 class Batch:
-    """Members (Solver objects) advanced together by dugks_batch_step."""
+    """Members (Solver objects) advanced together by dugks_batch_step.
+    persistent: K steps of each kernel group per launch, else (the default)
+    one grid launch per group and step (dugks_batch_set_persistent)."""
 
-    def __init__(self, stream=None):
+    def __init__(self, stream=None, persistent=False):
         import torch
 
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -400,6 +403,10 @@ class Batch:
                "dugks_batch_create")
         self.h = h
         self.members = []
+        self.set_persistent(persistent)
+
+    def set_persistent(self, on):
+        _check(lib().dugks_batch_set_persistent(self.h, 1 if on else 0), "dugks_batch_set_persistent")
 
     def add(self, solver):
         _check(lib().dugks_batch_add(self.h, solver.h), "dugks_batch_add")

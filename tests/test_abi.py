@@ -113,6 +113,13 @@ def test_upwind_limits_rejected_without_gpu(lib):
     assert lib.dugks_workspace_bytes(ctypes.byref(p)) == 0
 
 
+def test_batch_calls_reject_a_null_batch(lib):
+    """The batch entry points check their handle before any device work."""
+    assert lib.dugks_batch_set_persistent(None, 1) == -1
+    assert lib.dugks_batch_step(None, 1) == -1
+    assert lib.dugks_batch_size(None) == -1
+
+
 def test_status_strings_cover_every_code(lib):
     for code, name in solver.STATUS.items():
         text = lib.dugks_status_string(code).decode()

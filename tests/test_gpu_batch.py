@@ -8,7 +8,10 @@ single-problem kernel run the same tile code but are compiled separately
 may fuse multiply-adds differently: the two paths agree to round-off, and
 both agree with the oracle (test_gpu_parity).  A member large enough to fill
 the GPU by itself (2048 tiles or more) is stepped by the single-problem kernel
-inside the batch and is bit-identical to stepping it alone."""
+inside the batch and is bit-identical to stepping it alone.  Batches advance
+by default with one grid launch per step; the persistent mode advances up to
+16 steps per launch, in which a tile waits only for its own member's previous
+step.  Both are checked against the oracle and against each other."""
 import numpy as np
 import pytest
 
@@ -56,13 +59,13 @@ def problems():
     return out
 
 
-def alone(S, cfg, f, steps):
+def alone(S, cfg, f, steps, persistent=False):
     """The problem stepped by itself in a batch of one."""
     import torch
 
     st = torch.cuda.Stream()
     with S.Solver(cfg, stream=st, **f) as s:
-        with S.Batch(stream=st) as b:
+        with S.Batch(stream=st, persistent=persistent) as b:
             b.add(s)
             b.step(steps)
             b.sync()
@@ -86,13 +89,14 @@ def assert_round_off(cfg, m, m0, what=""):
         assert err <= tol, (what, k, err)
 
 
-def test_batch_member_bit_identical_to_batch_of_one(S):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_member_bit_identical_to_batch_of_one(S, persistent):
     import torch
 
     probs = problems()
     st = torch.cuda.Stream()
     solvers = [S.Solver(c, stream=st, **f) for c, f in probs]
-    with S.Batch(stream=st) as b:
+    with S.Batch(stream=st, persistent=persistent) as b:
         for s in solvers:
             b.add(s)
         assert len(b) == len(solvers)
@@ -102,7 +106,7 @@ def test_batch_member_bit_identical_to_batch_of_one(S):
     for s, (c, f) in zip(solvers, probs):
         assert s.step_count == 7
         m, state = s.macros(), s.get_state()
-        m0, state0 = alone(S, c, f, 7)
+        m0, state0 = alone(S, c, f, 7, persistent)
         for k in m:
             assert np.array_equal(m[k], m0[k]), (c["nx"], c["ny"], k)
         assert np.array_equal(state, state0)
@@ -231,7 +235,8 @@ def test_server_retires_a_failing_problem(S):
     assert s["failed"] == 1 and s["solves"] == 5
 
 
-def test_batch_members_match_the_oracle(S):
+@pytest.mark.parametrize("persistent", [True, False])
+def test_batch_members_match_the_oracle(S, persistent):
     """Every member of a mixed batch against the FP64 oracle directly (not
     through the single-problem kernel): two batched steps, a membership change,
     then 17 steps (one replay of the 16-step graph and one single step).  FP64
@@ -245,7 +250,7 @@ def test_batch_members_match_the_oracle(S):
     st = torch.cuda.Stream()
     solvers = [S.Solver(c, stream=st, **f) for c, f in probs]
     late = len(probs) - 1
-    with S.Batch(stream=st) as b:
+    with S.Batch(stream=st, persistent=persistent) as b:
         for s in solvers[:late]:
             b.add(s)
         b.step(2)
@@ -272,3 +277,42 @@ def test_batch_members_match_the_oracle(S):
             assert np.abs(got["uy"] - ref["uy"]).max() <= 1e-7, what
             assert np.abs(got["p"] - ref["p"]).max() <= 1e-5, what
         s.close()
+
+
+def _mix_run(S, persistent, steps):
+    import torch
+
+    probs = problems()
+    # members of very different tile counts, so that small ones run ahead
+    cfg, f = W.spinodal(N=480)
+    probs.append((dict(cfg, precision="fp32"), f))
+    cfg, f = W.random_state(20, 9, seed=12)
+    probs.append((cfg, f))
+    st = torch.cuda.Stream()
+    solvers = [S.Solver(c, stream=st, **f) for c, f in probs]
+    with S.Batch(stream=st, persistent=persistent) as b:
+        for s in solvers:
+            b.add(s)
+        b.step(steps)
+        b.sync()
+    out = []
+    for s, (c, f) in zip(solvers, probs):
+        assert s.step_count == steps
+        out.append((c, s.macros(), s.get_state()))
+        s.close()
+    return out
+
+
+def test_persistent_and_grid_launches_agree(S):
+    """37 steps (two 16-step launches and five single ones) of a mix of 13
+    members from 1 to 900 tiles in both modes.  The two kernels run the same
+    tile code with the same descriptor constants but are compiled separately,
+    so they agree to round-off; the per-member queue order changes nothing
+    else."""
+    a = _mix_run(S, True, 37)
+    b = _mix_run(S, False, 37)
+    same = 0
+    for (c, m, st), (_, m0, st0) in zip(a, b):
+        assert_round_off(c, m, m0, ("modes", c["nx"], c["ny"]))
+        same += int(np.array_equal(st, st0))
+    print("\npersistent vs grid launches: %d of %d members bit-identical" % (same, len(a)), end="")
