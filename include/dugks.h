@@ -153,6 +153,16 @@ dugks_status dugks_set_velocity_field(dugks_handle h, const double *ux_cell, con
  * error.  Synchronises cuda_stream; allocates and frees 4 device bytes. */
 dugks_status dugks_check_bounded_wait(int64_t max_polls, void *cuda_stream);
 
+/* Self-check of the persistent batched launch's wait for a member's previous
+ * step (failure detection without a fault): launches one CTA that waits, with
+ * that kernel's wait function, on a step counter that nothing raises, giving
+ * up after budget_ns nanoseconds of sleeps (<= 0: the kernel's own budget,
+ * about 2 s).  Returns DUGKS_ERR_TIMEOUT when the wait ran out as designed
+ * (the CUDA context stays usable), DUGKS_OK if it unexpectedly completed, or
+ * a CUDA error.  Synchronises cuda_stream; allocates and frees 8 device
+ * bytes. */
+dugks_status dugks_check_batch_wait(int64_t budget_ns, void *cuda_stream);
+
 /* Tile shapes the step kernels are compiled for, for one precision: writes
  * up to `cap` (tx, ty) cell counts (tx may be NULL, likewise ty) and returns
  * how many there are (tile_shape k >= 1 selects entry k - 1), or -1 for an

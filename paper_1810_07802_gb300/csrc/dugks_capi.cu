@@ -36,6 +36,14 @@ __global__ void wait_probe_kernel(long max_polls, unsigned *status) {
     }
 }
 
+// Self-check of the persistent batched kernel's wait for a member's previous
+// step: one thread waits, with the kernel's wait function, for one tile of a
+// member whose counter (*ctr, cleared by the caller) nothing raises, giving up
+// after budget_ns of sleeps, and records the timeout in *status.
+__global__ void batch_wait_probe_kernel(unsigned long long budget_ns, const unsigned *ctr, unsigned *status) {
+    if (threadIdx.x == 0 && !member_wait(ctr, 1u, 1u, budget_ns)) atomicOr(status, STATUS_TIMEOUT);
+}
+
 // Rows [row0, row0 + nrows) of the stored state (nq distribution planes, then
 // the 2 history planes, elements of T) to or from a contiguous buffer
 // [nq + 2][nrows][nx].  One thread per element; the grid covers the buffer.
@@ -604,6 +612,25 @@ dugks_status dugks_check_bounded_wait(int64_t max_polls, void *cuda_stream) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return from_cuda(e);
+    return (h & dugks::STATUS_TIMEOUT) ? DUGKS_ERR_TIMEOUT : DUGKS_OK;
+}
+
+dugks_status dugks_check_batch_wait(int64_t budget_ns, void *cuda_stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const unsigned long long budget = budget_ns > 0 ? (unsigned long long)budget_ns : dugks::kItemWaitNs;
+    unsigned *d = nullptr;   // [0]: the counter nothing raises, [1]: status
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(unsigned));
+    if (e != cudaSuccess) return from_cuda(e);
+    unsigned h = 0;
+    e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        dugks::batch_wait_probe_kernel<<<1, 32, 0, st>>>(budget, d, d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d + 1, sizeof h, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d);
     if (e != cudaSuccess) return from_cuda(e);

@@ -1613,6 +1613,23 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 #endif
 }
 
+// Waits until *done >= need (a member's counter; nt of its tiles per step),
+// sleeping in proportion to how many steps the member is behind, so that
+// CTAs waiting many steps ahead do not crowd the counter.  Returns false if
+// budget_ns of sleeps pass first.
+__device__ __forceinline__ bool member_wait(const unsigned *done, unsigned need, unsigned nt,
+                                            unsigned long long budget_ns) {
+    unsigned long long slept = 0;
+    for (unsigned have; (have = ld_acquire_gpu(done)) < need;) {
+        if (slept > budget_ns) return false;
+        const unsigned behind = (need - have + nt - 1) / nt;
+        const unsigned ns = behind > 1 ? (behind < 16 ? 1000u * (behind - 1) : 15000u) : 100u;
+        __nanosleep(ns);
+        slept += ns;
+    }
+    return true;
+}
+
 template <typename Real, int TX, int TY, bool COUPLED, bool WALLY, bool UPW = false>
 __global__ void __launch_bounds__((TileShape<Real, TX, TY, COUPLED, UPW>::NT),
                                   (TileShape<Real, TX, TY, COUPLED, UPW>::MINB))
@@ -1636,22 +1653,8 @@ persistent_step_kernel(const InstDesc<Real> *__restrict__ descs, const int2 *__r
         const InstDesc<Real> *d = descs + item.x;
         if (tid == 0) {
             const unsigned *done = ctr + 1 + item.x;
-            if (s > 0) {
-                const unsigned nt = (unsigned)d->ntiles, need = s * nt;
-                unsigned long long slept = 0;
-                for (unsigned have; (have = ld_acquire_gpu(done)) < need;) {
-                    if (slept > kItemWaitNs) {
-                        atomicOr(d->status, STATUS_TIMEOUT);
-                        break;
-                    }
-                    // back off by the member's distance in steps, so that CTAs
-                    // waiting many steps ahead do not crowd the counter
-                    const unsigned behind = (need - have + nt - 1) / nt;
-                    const unsigned ns = behind > 1 ? (behind < 16 ? 1000u * (behind - 1) : 15000u) : 100u;
-                    __nanosleep(ns);
-                    slept += ns;
-                }
-            }
+            const unsigned nt = (unsigned)d->ntiles;
+            if (s > 0 && !member_wait(done, s * nt, nt, kItemWaitNs)) atomicOr(d->status, STATUS_TIMEOUT);
             fence_proxy_async_global();
         }
         __syncthreads();

@@ -67,6 +67,7 @@ SIGNATURES = {
     "dugks_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "dugks_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "dugks_check_batch_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
     "dugks_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_check_bounded_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
     "dugks_set_velocity_field": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
@@ -158,6 +159,13 @@ def check_bounded_wait(max_polls=0, stream=None):
     wait ran out as designed)."""
     return int(lib().dugks_check_bounded_wait(int(max_polls),
                                               ctypes.c_void_p(stream.cuda_stream) if stream is not None else None))
+
+
+def check_batch_wait(budget_ns=0, stream=None):
+    """Runs the persistent batched launch's wait self-check; returns the
+    status code (-6 = the wait ran out as designed)."""
+    return int(lib().dugks_check_batch_wait(int(budget_ns),
+                                            ctypes.c_void_p(stream.cuda_stream) if stream is not None else None))
 
 
 def tile_shapes(precision="fp32"):

@@ -316,3 +316,36 @@ def test_persistent_and_grid_launches_agree(S):
         assert_round_off(c, m, m0, ("modes", c["nx"], c["ny"]))
         same += int(np.array_equal(st, st0))
     print("\npersistent vs grid launches: %d of %d members bit-identical" % (same, len(a)), end="")
+
+
+def test_persistent_wait_times_out_and_batches_still_run(S):
+    """Failure detection without a fault: the persistent launch's wait for a
+    member's previous step, run on a counter that nothing raises, gives up
+    after its sleep budget (the kernel's own, about 2 s, and a short one); the
+    host reads DUGKS_ERR_TIMEOUT and a persistent batch then still matches the
+    oracle."""
+    import time
+
+    from oracle.oracle import Oracle
+
+    t0 = time.perf_counter()
+    assert S.check_batch_wait() == -6
+    waited = time.perf_counter() - t0
+    assert 1.0 < waited < 10.0, waited
+    assert S.check_batch_wait(budget_ns=1000000) == -6
+    cfg, f = W.random_state(40, 30, seed=8)
+    import torch
+
+    st = torch.cuda.Stream()
+    with S.Solver(cfg, stream=st, **f) as s:
+        with S.Batch(stream=st, persistent=True) as b:
+            b.add(s)
+            b.step(18)
+            b.sync()
+            b.remove(s)
+        got = s.macros()
+    o = Oracle(cfg, **f)
+    o.step(18)
+    ref = o.macros()
+    for k in ("phi", "p", "ux", "uy"):
+        assert np.abs(got[k] - ref[k]).max() <= 1e-10, k
