@@ -213,6 +213,21 @@ dugks_status dugks_macros(dugks_handle h, double *phi, double *p, double *ux, do
 dugks_status dugks_reduce(dugks_handle h, double *phi_mass, double *resid_phi,
                           double *resid_u, double *umax);
 
+/* The sums behind dugks_reduce over the rows [row0, row0 + nrows) only, for
+ * combining several y-bands of one problem (sum the first five over bands,
+ * take the maximum of the last, then form the Eq. 44 ratios sums[2]/sums[1]
+ * and sums[4]/sums[3]): sums[0] = sum phi, sums[1] = sum phi^2, sums[2] =
+ * sum (phi - phi_prev)^2, sums[3] = sum |u|^2, sums[4] = sum |u - u_prev|^2,
+ * sums[5] = max |u|, in FP64 on the device, the previous fields being those
+ * of the last dugks_reduce / dugks_reduce_rows call on the handle
+ * (*had_snapshot = 0 and sums[2] = sums[4] = 0 on the first call;
+ * had_snapshot may be NULL).  Like dugks_reduce it then keeps the whole
+ * grid's fields as the next call's previous fields.  DUGKS_ERR_ARG for rows
+ * outside the grid or a NULL sums; a failed step is reported as by
+ * dugks_reduce, with the sums written.  Synchronises. */
+dugks_status dugks_reduce_rows(dugks_handle h, int32_t row0, int32_t nrows, double *sums,
+                               int32_t *had_snapshot);
+
 /* The distributions as absolute FP64 values, in the oracle-comparable layout:
  * f [9][ny][nx], g [9][ny][nx] (zero for the Allen-Cahn-only model) and the
  * stored (phi u)^{n-1} [2][ny][nx], on the host; any pointer may be NULL.

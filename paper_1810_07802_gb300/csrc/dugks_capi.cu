@@ -77,8 +77,8 @@ cudaError_t launch_rows(void *state, void *hist, size_t elt, int nq, int pitch, 
 }
 
 cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
-                          int have_snap, double *partial, double *out, cudaStream_t st) {
-    reduce_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(phi, ux, uy, snap, n, have_snap, partial);
+                          long long sstride, int have_snap, double *partial, double *out, cudaStream_t st) {
+    reduce_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(phi, ux, uy, snap, n, sstride, have_snap, partial);
     reduce_final_kernel<<<1, 32, 0, st>>>(partial, out);
     return cudaGetLastError();
 }
@@ -435,28 +435,59 @@ dugks_status dugks_macros(dugks_handle c, double *phi, double *p, double *ux, do
     return sync_status(c);
 }
 
-dugks_status dugks_reduce(dugks_handle c, double *phi_mass, double *resid_phi, double *resid_u, double *umax) {
-    dugks::TraceRange trace_("dugks_reduce");
-    if (!c) return DUGKS_ERR_ARG;
+namespace {
+// The FP64 sums of the macros over rows [row0, row0 + nrows) against the
+// snapshot the previous reduction left, into r[RED_VALS] (*filled = 1 once
+// they are there, also when the status word reports a failed step); then the
+// whole grid becomes the new snapshot.  Synchronises.
+dugks_status reduce_sums(dugks_handle c, int32_t row0, int32_t nrows, double *r, int *had_snap, int *filled) {
+    *filled = 0;
     double *s = c->stage();
-    const size_t n = c->L.n;
+    const size_t n = c->L.n, off = (size_t)row0 * c->P.nx, m = (size_t)nrows * c->P.nx;
     cudaError_t e = run_macros(c, s, s + n, s + 2 * n, s + 3 * n);
     if (e == cudaSuccess)
-        e = dugks::launch_reduce(s, s + 2 * n, s + 3 * n, c->snap(), (long long)n, c->have_snap, c->partial(),
-                                 c->redout(), c->st);
-    double r[dugks::RED_VALS];
+        e = dugks::launch_reduce(s + off, s + 2 * n + off, s + 3 * n + off, c->snap() + off, (long long)m,
+                                 (long long)n, c->have_snap, c->partial(), c->redout(), c->st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(r, c->redout(), sizeof r, cudaMemcpyDeviceToHost, c->st);
+        e = cudaMemcpyAsync(r, c->redout(), dugks::RED_VALS * sizeof(double), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->snap(), s, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->snap() + n, s + 2 * n, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     if (e != cudaSuccess) return from_cuda(e);
     dugks_status st = sync_status(c);
-    if (phi_mass) *phi_mass = r[0];
-    if (resid_phi) *resid_phi = c->have_snap ? (r[1] > 0 ? r[2] / r[1] : 0.0) : 1.0;
-    if (resid_u) *resid_u = c->have_snap ? (r[3] > 0 ? r[4] / r[3] : 0.0) : 1.0;
-    if (umax) *umax = r[5];
+    if (st == DUGKS_ERR_CUDA) return st;
+    *filled = 1;
+    *had_snap = c->have_snap;
     c->have_snap = 1;
+    return st;
+}
+}  // namespace
+
+dugks_status dugks_reduce_rows(dugks_handle c, int32_t row0, int32_t nrows, double *sums, int32_t *had_snapshot) {
+    dugks::TraceRange trace_("dugks_reduce_rows");
+    if (!c || !sums || nrows < 1 || row0 < 0 || row0 + nrows > c->P.ny) return DUGKS_ERR_ARG;
+    double r[dugks::RED_VALS];
+    int had = 0, filled = 0;
+    dugks_status st = reduce_sums(c, row0, nrows, r, &had, &filled);
+    if (!filled) return st;
+    // [0] sum phi, [1] sum phi^2, [2] sum dphi^2, [3] sum |u|^2, [4] sum |du|^2, [5] max |u|
+    for (int i = 0; i < dugks::RED_VALS; i++) sums[i] = r[i];
+    if (!had) sums[2] = sums[4] = 0.0;
+    if (had_snapshot) *had_snapshot = had;
+    return st;
+}
+
+dugks_status dugks_reduce(dugks_handle c, double *phi_mass, double *resid_phi, double *resid_u, double *umax) {
+    dugks::TraceRange trace_("dugks_reduce");
+    if (!c) return DUGKS_ERR_ARG;
+    double r[dugks::RED_VALS];
+    int had = 0, filled = 0;
+    dugks_status st = reduce_sums(c, 0, c->P.ny, r, &had, &filled);
+    if (!filled) return st;
+    if (phi_mass) *phi_mass = r[0];
+    if (resid_phi) *resid_phi = had ? (r[1] > 0 ? r[2] / r[1] : 0.0) : 1.0;
+    if (resid_u) *resid_u = had ? (r[3] > 0 ? r[4] / r[3] : 0.0) : 1.0;
+    if (umax) *umax = r[5];
     return st;
 }
 

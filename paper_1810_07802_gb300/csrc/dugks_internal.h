@@ -41,7 +41,7 @@ template <typename Real>
 cudaError_t launch_batch_step(int tile, bool upw, InstDesc<Real> *descs, const int2 *work, int nwork, int ninst,
                               bool coupled, bool wally, int ksteps, unsigned *ctr, cudaStream_t st);
 cudaError_t launch_reduce(const double *phi, const double *ux, const double *uy, const double *snap, long long n,
-                          int have_snap, double *partial, double *out, cudaStream_t st);
+                          long long sstride, int have_snap, double *partial, double *out, cudaStream_t st);
 
 
 // Workspace layout of one solver (offsets in bytes, 256-byte aligned regions).

@@ -23,11 +23,14 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// Block b reduces cells b, b + RED_BLOCKS*RED_THREADS, ... of the [ny][nx]
-// macro planes into partial[b][RED_VALS].  have_snap = 0 skips the residual sums.
+// Block b reduces cells b, b + RED_BLOCKS*RED_THREADS, ... of n consecutive
+// cells of the [ny][nx] macro planes into partial[b][RED_VALS]; the snapshot
+// holds phi, ux, uy at snap, snap + sstride, snap + 2 sstride (sstride = n
+// for a whole grid).  have_snap = 0 skips the residual sums.
 __global__ void __launch_bounds__(RED_THREADS)
 reduce_partial_kernel(const double *__restrict__ phi, const double *__restrict__ ux, const double *__restrict__ uy,
-                      const double *__restrict__ snap, long long n, int have_snap, double *__restrict__ partial) {
+                      const double *__restrict__ snap, long long n, long long sstride, int have_snap,
+                      double *__restrict__ partial) {
     __shared__ double red[RED_VALS][RED_THREADS / 32];
     double v[RED_VALS] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (long long c = (long long)blockIdx.x * RED_THREADS + threadIdx.x; c < n; c += (long long)RED_BLOCKS * RED_THREADS) {
@@ -38,7 +41,7 @@ reduce_partial_kernel(const double *__restrict__ phi, const double *__restrict__
         v[3] += u2;
         v[5] = fmax(v[5], sqrt(u2));
         if (have_snap) {
-            const double dp = p - snap[c], da = a - snap[n + c], db = b - snap[2 * n + c];
+            const double dp = p - snap[c], da = a - snap[sstride + c], db = b - snap[2 * sstride + c];
             v[2] += dp * dp;
             v[4] += da * da + db * db;
         }

@@ -14,8 +14,14 @@ The exchange is a pair of point-to-point messages per neighbour, no
 collective: LocalExchange moves rows between bands held by one process
 (one device), DistExchange between ranks over torch.distributed (NCCL
 between GPUs; gloo on the CPU).  A band stepper is anything with
-row_buffer(nrows), get_rows(row0, nrows, buf), set_rows(row0, nrows, buf)
-and step(n): the GPU Solver of this package is one.
+row_buffer(nrows), get_rows(row0, nrows, buf), set_rows(row0, nrows, buf),
+step(n) and reduce_rows(row0, nrows): the GPU Solver of this package is one.
+
+The FP64 reductions of the whole problem (phi mass, the steady-state
+residuals of Eq. 44, max |u|) come from each band's sums over its own rows,
+taken after a halo exchange: five sums added over the bands and one maximum
+(an all-reduce of six numbers between ranks), then the ratios the
+single-domain reduction forms.
 """
 import numpy as np
 
@@ -63,6 +69,36 @@ class Band:
         self.stepper.set_rows(0, HALO, self.recv_below)
         self.stepper.set_rows(HALO + self.n_own, HALO, self.recv_above)
 
+    def sums(self):
+        """The band's reduction sums over its own rows (see combine)."""
+        return self.stepper.reduce_rows(HALO, self.n_own)
+
+
+def combine(sums, had_snapshot):
+    """(phi mass, phi residual, u residual, max |u|) of the whole problem from
+    the bands' summed sums [sum phi, sum phi^2, sum dphi^2, sum |u|^2,
+    sum |du|^2] and the largest max |u|, as the single-domain reduction forms
+    them (residuals 1.0 without a previous reduction)."""
+    s = [float(x) for x in sums]
+    if not had_snapshot:
+        return s[0], 1.0, 1.0, s[5]
+    rphi = s[2] / s[1] if s[1] > 0 else 0.0
+    ru = s[4] / s[3] if s[3] > 0 else 0.0
+    return s[0], rphi, ru, s[5]
+
+
+def reduce_local(exchange, band_list):
+    """The whole problem's reductions from bands held by one process.  The
+    halo rows are refreshed first: u at a band's edge rows needs the
+    gradient of phi across them."""
+    exchange()
+    parts = [b.sums() for b in band_list]
+    tot = np.zeros(6)
+    for v, _ in parts:
+        tot[:5] += v[:5]
+        tot[5] = max(tot[5], v[5])
+    return combine(tot, all(h for _, h in parts))
+
 
 class LocalExchange:
     """Halo exchange between the bands of one process, in ring order (band b's
@@ -106,6 +142,23 @@ class DistExchange:
         for req in dist.batch_isend_irecv(ops):
             req.wait()
         b.unpack()
+
+    def reduce(self):
+        """The whole problem's reductions: this rank's band sums, all-reduced
+        (a sum of five, a maximum of one) over the ranks, after a halo
+        exchange (u at the band's edge rows needs phi across them)."""
+        import torch
+        import torch.distributed as dist
+
+        self()
+        v, had = self.band.sums()
+        dev = "cuda" if dist.get_backend(self.group) == "nccl" else "cpu"
+        t = torch.tensor(list(v[:5]) + [1.0 if had else 0.0], dtype=torch.float64, device=dev)
+        m = torch.tensor([v[5]], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX, group=self.group)
+        t, m = t.cpu().numpy(), m.cpu().numpy()
+        return combine(list(t[:5]) + [m[0]], t[5] == self.world)
 
 
 def step_bands(exchange, band_list, n):

@@ -68,6 +68,8 @@ SIGNATURES = {
     "dugks_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "dugks_check_batch_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
+    "dugks_reduce_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "dugks_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "dugks_check_bounded_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
     "dugks_set_velocity_field": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
@@ -350,6 +352,16 @@ class Solver:
         v = [ctypes.c_double() for _ in range(4)]
         _check(lib().dugks_reduce(self.h, *[ctypes.byref(x) for x in v]), "dugks_reduce")
         return tuple(x.value for x in v)
+
+    def reduce_rows(self, row0, nrows):
+        """The sums behind reduce() over rows [row0, row0 + nrows):
+        (array [sum phi, sum phi^2, sum dphi^2, sum |u|^2, sum |du|^2, max |u|],
+        whether there was a previous reduction to difference against)."""
+        sums = np.zeros(6)
+        had = ctypes.c_int32()
+        _check(lib().dugks_reduce_rows(self.h, int(row0), int(nrows), _ptr(sums), ctypes.byref(had)),
+               "dugks_reduce_rows")
+        return sums, bool(had.value)
 
     def distributions(self):
         f = np.empty((9, self.ny, self.nx))

@@ -146,3 +146,51 @@ def test_row_copies_round_trip_and_reject_bad_rows(S):
             s.get_rows(18, 3, buf)
         with pytest.raises(ValueError):
             s.get_rows(0, 2, buf)
+
+
+def test_reduce_rows_over_every_row_is_reduce(S):
+    """dugks_reduce_rows over all rows, combined, is dugks_reduce bit for bit
+    (the same kernel over the same cells), with and without a previous call."""
+    from paper_1810_07802_gb300 import slab
+
+    cfg, f = W.random_state(150, 70, seed=31, rho_ratio=100.0)
+    with S.Solver(cfg, **f) as a, S.Solver(cfg, **f) as b:
+        for n in (3, 4):
+            a.step(n)
+            b.step(n)
+            want = a.reduce()
+            sums, had = b.reduce_rows(0, cfg["ny"])
+            assert slab.combine(sums, had) == want
+        with pytest.raises(S.DugksError):
+            b.reduce_rows(60, 11)
+
+
+def test_band_reductions_equal_the_single_domain(S):
+    """phi mass, the Eq. 44 residuals and max |u| of three FP64 bands, from
+    their own-row sums after a halo exchange, against the single-domain
+    solver's reduction, after 7 steps (no previous fields) and 3 more."""
+    from paper_1810_07802_gb300 import slab
+
+    cfg, f = W.random_state(150, 70, seed=31, rho_ratio=100.0)
+    with S.Solver(cfg, **f) as whole:
+        whole.step(7)
+        want = [whole.reduce()]
+        whole.step(3)
+        want.append(whole.reduce())
+    band_list = []
+    for r0, r1 in slab.bands(cfg["ny"], 3):
+        bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
+        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1))
+    ex = slab.LocalExchange(band_list)
+    slab.step_bands(ex, band_list, 7)
+    got = [slab.reduce_local(ex, band_list)]
+    slab.step_bands(ex, band_list, 3)
+    got.append(slab.reduce_local(ex, band_list))
+    for b in band_list:
+        b.stepper.close()
+    for (m, rp, ru, um), (m0, rp0, ru0, um0) in zip(got, want):
+        assert m == pytest.approx(m0, rel=1e-13)
+        assert rp == pytest.approx(rp0, rel=1e-9)
+        assert ru == pytest.approx(ru0, rel=1e-9)
+        assert um == pytest.approx(um0, rel=1e-12)
+    assert got[0][1] == 1.0 and got[1][1] < 1.0

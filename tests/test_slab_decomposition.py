@@ -68,6 +68,22 @@ class OracleBand:
         self.o.step(n)
         self.n += n
 
+    def reduce_rows(self, row0, nrows):
+        """The sums behind the oracle's reduction over rows [row0, row0 + nrows),
+        against the whole grid kept at the previous call (numpy, FP64)."""
+        m = self.o.macros()
+        phi, ux, uy = m["phi"], m["ux"], m["uy"]
+        rows = slice(row0, row0 + nrows)
+        u2 = ux[rows] ** 2 + uy[rows] ** 2
+        sums = np.array([phi[rows].sum(), (phi[rows] ** 2).sum(), 0.0, u2.sum(), 0.0, np.sqrt(u2).max()])
+        had = getattr(self, "_snap", None) is not None
+        if had:
+            p0, a0, b0 = self._snap
+            sums[2] = ((phi[rows] - p0[rows]) ** 2).sum()
+            sums[4] = ((ux[rows] - a0[rows]) ** 2 + (uy[rows] - b0[rows]) ** 2).sum()
+        self._snap = (phi.copy(), ux.copy(), uy.copy())
+        return sums, had
+
 
 def _problem():
     from paper_1810_07802_gb300 import workloads as W
@@ -85,21 +101,43 @@ def _rank_main(rank, world, port, steps, q):
         cfg, fl = _problem()
         r0, r1 = slab.bands(cfg["ny"], world)[rank]
         band = slab.Band(OracleBand(*slab.band_problem(cfg, fl, r0, r1)), r0, r1)
-        slab.step_bands(slab.DistExchange(band, rank, world), [band], steps)
+        ex = slab.DistExchange(band, rank, world)
+        slab.step_bands(ex, [band], steps)
+        red = [ex.reduce()]
+        slab.step_bands(ex, [band], 3)
+        red.append(ex.reduce())
+        slab.step_bands(ex, [band], 1)   # the halo exchange before the next step: band state = after steps + 4
         f, g, h = band.stepper.o.state()
         own = slice(HALO, HALO + band.n_own)
-        q.put((rank, r0, r1, f[:, own].copy(), g[:, own].copy(), h[:, own].copy()))
+        q.put((rank, r0, r1, f[:, own].copy(), g[:, own].copy(), h[:, own].copy(), red))
     finally:
         dist.destroy_process_group()
 
 
 def _single_domain(steps):
+    """The single-domain oracle after steps + 4 steps, with its reductions
+    after `steps` and after `steps` + 3."""
     from oracle.oracle import Oracle
 
     cfg, fl = _problem()
     ref = Oracle(cfg, **fl)
     ref.step(steps)
-    return cfg, ref.state()
+    red = [ref.reduce()]
+    ref.step(3)
+    red.append(ref.reduce())
+    ref.step(1)
+    return cfg, ref.state(), red
+
+
+def _assert_same_reductions(got, want):
+    """phi mass, both residuals and max |u| of the bands against the single
+    domain (the sums run over the cells in another order)."""
+    for (m, rp, ru, um), (m0, rp0, ru0, um0) in zip(got, want):
+        assert m == pytest.approx(m0, rel=1e-13)
+        assert rp == pytest.approx(rp0, rel=1e-10)
+        assert ru == pytest.approx(ru0, rel=1e-10)
+        assert um == um0
+    assert got[0][1] == 1.0 and got[1][1] < 1.0
 
 
 @pytest.mark.parametrize("world", [2, 3])
@@ -117,9 +155,10 @@ def test_slabs_with_halo_exchange_equal_the_single_domain(world):
     for p in procs:
         p.join(60)
         assert p.exitcode == 0
-    cfg, (F, G, H) = _single_domain(steps)
+    cfg, (F, G, H), red = _single_domain(steps)
     covered = np.zeros(cfg["ny"], dtype=int)
-    for rank, r0, r1, f, g, h in parts:
+    for rank, r0, r1, f, g, h, band_red in parts:
+        _assert_same_reductions(band_red, red)
         assert np.array_equal(f, F[:, r0:r1]), rank
         assert np.array_equal(g, G[:, r0:r1]), rank
         assert np.array_equal(h, H[:, r0:r1]), rank
@@ -134,8 +173,14 @@ def test_local_exchange_of_three_bands():
     cfg, fl = _problem()
     band_list = [slab.Band(OracleBand(*slab.band_problem(cfg, fl, r0, r1)), r0, r1)
                  for r0, r1 in slab.bands(cfg["ny"], 3)]
-    slab.step_bands(slab.LocalExchange(band_list), band_list, steps)
-    _, (F, G, H) = _single_domain(steps)
+    ex = slab.LocalExchange(band_list)
+    slab.step_bands(ex, band_list, steps)
+    red = [slab.reduce_local(ex, band_list)]
+    slab.step_bands(ex, band_list, 3)
+    red.append(slab.reduce_local(ex, band_list))
+    slab.step_bands(ex, band_list, 1)
+    _, (F, G, H), red0 = _single_domain(steps)
+    _assert_same_reductions(red, red0)
     for b in band_list:
         f, g, h = b.stepper.o.state()
         own = slice(HALO, HALO + b.n_own)
