@@ -1,7 +1,8 @@
-"""The y-slab decomposition on the GPU: bands of one periodic problem, each a
-Solver on its rows plus two halo rows per side, their halo rows refreshed
-before every step through dugks_get_rows / dugks_set_rows (device buffers,
-exchanged in one process).  (With one GPU per box the same bands over NCCL
+"""The y-slab decomposition on the GPU: bands of one problem (periodic or
+walled in y), each a Solver on its rows plus two halo rows (three with the
+upwind reconstruction) on each side that has a neighbour, their halo rows
+refreshed before every step through dugks_get_rows / dugks_set_rows (device
+buffers, exchanged in one process).  (With one GPU per box the same bands over NCCL
 between GPUs are not run here; the exchange protocol on ranks is covered with
 gloo in test_slab_decomposition, bit for bit against the oracle.)
 
@@ -52,13 +53,13 @@ def test_bands_equal_the_single_domain(S, precision, world):
     band_list = []
     for r0, r1 in slab.bands(cfg["ny"], world):
         bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
-        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1))
+        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1, cfg))
     slab.step_bands(slab.LocalExchange(band_list), band_list, steps)
     worst = 0.0
     covered = np.zeros(cfg["ny"], dtype=int)
     for b in band_list:
         got = b.stepper.distributions()
-        own = slice(slab.HALO, slab.HALO + b.n_own)
+        own = b.own
         for g, r in zip(got, ref):
             worst = max(worst, float(np.abs(g[:, own] - r[:, b.r0:b.r1]).max()))
         covered[b.r0:b.r1] += 1
@@ -84,7 +85,7 @@ def test_a_stale_halo_row_is_far_above_the_bound(S):
     band_list = []
     for r0, r1 in slab.bands(cfg["ny"], 2):
         bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
-        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1))
+        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1, cfg))
     exchange = slab.LocalExchange(band_list)
     b0 = band_list[0]
     row = b0.stepper.row_buffer(1)
@@ -97,7 +98,7 @@ def test_a_stale_halo_row_is_far_above_the_bound(S):
 
     slab.step_bands(faulty, band_list, steps)
     got = b0.stepper.distributions()
-    own = slice(slab.HALO, slab.HALO + b0.n_own)
+    own = b0.own
     err = max(float(np.abs(g[:, own] - r[:, b0.r0:b0.r1]).max()) for g, r in zip(got, ref))
     print("\nstale halo row: max |band - single domain| %.2e" % err, end="")
     for b in band_list:
@@ -105,27 +106,58 @@ def test_a_stale_halo_row_is_far_above_the_bound(S):
     assert err > 1e3 * ROUNDOFF["fp64"], err
 
 
-def test_fp64_bands_match_the_oracle(S):
-    """FP64 bands against the single-domain FP64 oracle at the parity bar."""
+@pytest.mark.parametrize("kind", ["periodic", "wall", "upwind", "wall_upwind"])
+def test_fp64_bands_match_the_oracle(S, kind):
+    """FP64 bands against the single-domain FP64 oracle at the parity bar:
+    periodic and walled problems (walled bands: no halo at the problem's
+    walls, the bands' inner walls beyond their halo rows), with the central
+    reconstruction (two halo rows) and the upwind one (three)."""
     from oracle.oracle import Oracle
     from paper_1810_07802_gb300 import slab
 
-    cfg, f = W.random_state(150, 70, seed=31, rho_ratio=100.0)
+    cfg, f = W.random_state(150, 70, seed=31, rho_ratio=100.0, bc_y="wall" if "wall" in kind else "periodic")
+    if "upwind" in kind:
+        cfg = dict(cfg, recon="upwind")
     steps = 7
     ref = Oracle(cfg, **f)
     ref.step(steps)
     F, G, Hh = ref.state()
     band_list = []
-    for r0, r1 in slab.bands(cfg["ny"], 3):
+    for r0, r1 in slab.bands(cfg["ny"], 3, slab.halo_rows(cfg)):
         bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
-        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1))
+        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1, cfg))
     slab.step_bands(slab.LocalExchange(band_list), band_list, steps)
     for b in band_list:
         got = b.stepper.distributions()
-        own = slice(slab.HALO, slab.HALO + b.n_own)
+        own = b.own
         for g, r in zip(got, (F, G, Hh)):
-            assert np.abs(g[:, own] - r[:, b.r0:b.r1]).max() <= 1e-10
+            assert np.abs(g[:, own] - r[:, b.r0:b.r1]).max() <= 1e-10, (kind, b.r0)
         b.stepper.close()
+
+
+def test_fp32_walled_bands_equal_the_single_domain(S):
+    """FP32-shifted bands of a walled problem against the single-domain FP32
+    solver, to the round-off bound of the periodic case."""
+    from paper_1810_07802_gb300 import slab
+
+    cfg, f = W.random_state(150, 70, seed=31, rho_ratio=100.0, bc_y="wall")
+    cfg = dict(cfg, precision="fp32", phi_ref=0.5)
+    with S.Solver(cfg, **f) as whole:
+        whole.step(7)
+        ref = whole.distributions()
+    band_list = []
+    for r0, r1 in slab.bands(cfg["ny"], 3):
+        bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
+        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1, cfg))
+    assert band_list[0].lo == 0 and band_list[-1].hi == 0
+    slab.step_bands(slab.LocalExchange(band_list), band_list, 7)
+    worst = 0.0
+    for b in band_list:
+        for g, r in zip(b.stepper.distributions(), ref):
+            worst = max(worst, float(np.abs(g[:, b.own] - r[:, b.r0:b.r1]).max()))
+        b.stepper.close()
+    print("\nfp32 walled, 3 bands: max |band - single domain| %.2e" % worst, end="")
+    assert worst <= ROUNDOFF["fp32"], worst
 
 
 def test_row_copies_round_trip_and_reject_bad_rows(S):
@@ -180,7 +212,7 @@ def test_band_reductions_equal_the_single_domain(S):
     band_list = []
     for r0, r1 in slab.bands(cfg["ny"], 3):
         bcfg, bfields = slab.band_problem(cfg, f, r0, r1)
-        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1))
+        band_list.append(slab.Band(S.Solver(bcfg, **bfields), r0, r1, cfg))
     ex = slab.LocalExchange(band_list)
     slab.step_bands(ex, band_list, 7)
     got = [slab.reduce_local(ex, band_list)]
