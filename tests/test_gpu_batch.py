@@ -187,7 +187,11 @@ def test_batch_membership_changes(S):
         s.close()
 
 
-def test_serving_results_identical_alone_and_in_the_mix(S):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_serving_results_identical_alone_and_in_the_mix(S, persistent):
+    """Continuous batching (grid or persistent batch launches): each served
+    result is bit-identical to the same problem in a batch of one of the same
+    mode, and agrees to round-off with the one-at-a-time server."""
     from paper_1810_07802_gb300.serve import BatchingServer, Request, SequentialServer, summary
 
     trace = W.serving_trace(n=10, rate=400.0, seed=5, steps={"poiseuille": 30, "bubble": 20, "spinodal": 15})
@@ -197,11 +201,11 @@ def test_serving_results_identical_alone_and_in_the_mix(S):
             cfg, f = W.spinodal(N=128, seed=99 + i)
             cfg["precision"] = "fp32"
         small.append(Request(i, kind, cfg, f, steps, t))
-    srv = BatchingServer(hbm_budget=8 << 30, max_members=6, chunk=8)
+    srv = BatchingServer(hbm_budget=8 << 30, max_members=6, chunk=8, persistent=persistent)
     recs = srv.run(small)
     assert len(recs) == len(small)
     for r, q in zip(recs, small):
-        m0, _ = alone(S, q.cfg, q.fields, q.steps)
+        m0, _ = alone(S, q.cfg, q.fields, q.steps, persistent)
         for k in m0:
             assert np.array_equal(r.result[k], m0[k]), (q.rid, k)
     s = summary(recs)
