@@ -161,6 +161,7 @@ template <typename Real>
 struct Pt {
     Real phi, dpx, dpy, lap;
     Real rho, irho, drx, dry, taug;
+    Real inv;                 // FP64: 1 / (2 tau_g + step), see closures
     Real theta, nx, ny;
     Real Fx, Fy, ux, uy, pd;  // pd = p - p_ref
     Real Dx, Dy;
@@ -219,9 +220,11 @@ __device__ __forceinline__ void prescribed_velocity(const Phys<Real> &ph, Real x
 }
 
 // theta, n (Eq. 6) and, for the coupled model, rho, mu_phi, mu, tau_g and F
-// (Eqs. 3-4, 9-10, 34-36) from phi, grad phi and lap phi.
+// (Eqs. 3-4, 9-10, 34-36) from phi, grad phi and lap phi; in FP64 also
+// 1 / (2 tau_g + step), the factor of the relaxation (Eqs. 28-29: step = h at
+// a face, dt at a cell).
 template <typename Real, bool COUPLED>
-__device__ __forceinline__ void closures(const Phys<Real> &ph, Pt<Real> &s) {
+__device__ __forceinline__ void closures(const Phys<Real> &ph, Pt<Real> &s, Real step = Real(0)) {
     const Real phi = s.phi;
     s.theta = ph.theta_k * phi * (Real(1) - phi);
     const Real inv = rsqrt_r(s.dpx * s.dpx + s.dpy * s.dpy + Real(1e-16));
@@ -233,9 +236,25 @@ __device__ __forceinline__ void closures(const Phys<Real> &ph, Pt<Real> &s) {
         s.dry = ph.drho * s.dpy;
         const Real muphi = ph.beta4 * phi * (phi - Real(1)) * (phi - Real(0.5)) - ph.kappa * s.lap;
         const Real lin = ph.visc_a * phi + ph.visc_b;
-        const Real mu = ph.visc_linear ? lin : rcp_r(lin);
-        s.irho = rcp_r(s.rho);
-        s.taug = Real(3) * mu * s.irho;
+        if constexpr (sizeof(Real) == 8) {
+            // One FP64 division instead of three: with mu = num / den (linear rule
+            // lin / 1, reciprocal rule 1 / lin) and e = 6 num + step rho den
+            // (= (2 tau_g + step) rho den), R = 1 / (rho den e) gives 1 / rho =
+            // den e R, tau_g = 3 mu / rho = 3 num e R and 1 / (2 tau_g + step) =
+            // (rho den)^2 R.
+            const Real num = ph.visc_linear ? lin : Real(1), den = ph.visc_linear ? Real(1) : lin;
+            const Real rd = s.rho * den, e = Real(6) * num + step * rd;
+            const Real R = Real(1) / (rd * e);
+            const Real er = e * R;
+            s.irho = den * er;
+            s.taug = Real(3) * num * er;
+            s.inv = rd * rd * R;
+        } else {
+            const Real mu = ph.visc_linear ? lin : rcp_r(lin);
+            s.irho = rcp_r(s.rho);
+            s.taug = Real(3) * mu * s.irho;
+            s.inv = Real(0);   // FP32 takes its cheap reciprocal where the factor is used
+        }
         Real Gx = ph.gx, Gy = ph.gy;
         if (ph.grav_mode) {
             Gx = (s.rho - ph.rho_ref) * ph.gx;
@@ -901,7 +920,7 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
     s.lap = lap;
     s.Dx = Dx;
     s.Dy = Dy;
-    closures<Real, COUPLED>(ph, s);
+    closures<Real, COUPLED>(ph, s, ph.h);
     if constexpr (COUPLED) {
         Real mx, my, sn;
         moments9(gb, mx, my, sn);
@@ -928,7 +947,7 @@ __device__ __forceinline__ void face_flux(const Phys<Real> &ph, const Real fb[9]
         if (slot >= 0) out[slot] = ph.ff_a * fb[k] + f_lin_k(k, lf);
     }
     if (COUPLED) {
-        const Real inv = rcp_r(Real(2) * s.taug + ph.h);
+        const Real inv = sizeof(Real) == 8 ? s.inv : rcp_r(Real(2) * s.taug + ph.h);
         const Real a = Real(2) * s.taug * inv, bb = ph.h * inv, c = s.taug * ph.h * inv;
         const GLin<Real> gl = g_lin(s, bb, c);
 #pragma unroll
@@ -1004,7 +1023,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
     const int c2 = (hy + 1) * S::HX2 + (hx + 1);
     phi_stencils(sphi, c2, S::HX2, s.dpx, s.dpy, s.lap);
     s.phi = ph.phi_ref + sphi[c2];
-    closures<Real, COUPLED>(ph, s);
+    closures<Real, COUPLED>(ph, s, ph.dt);
     Real dg[9];
     if (COUPLED) {
 #pragma unroll
@@ -1094,7 +1113,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<Real> &a, const Phys<Re
         }
     }
     if (COUPLED) {
-        const Real inv = rcp_r(Real(2) * s.taug + ph.dt);
+        const Real inv = S::F64 ? s.inv : rcp_r(Real(2) * s.taug + ph.dt);
         const Real ca = (Real(2) * s.taug - ph.h) * inv, cb = Real(3) * ph.h * inv, cc = Real(3) * s.taug * ph.h * inv;
         const GLin<Real> gl = g_lin(s, cb, cc);
         if constexpr (DUGKS_PACKED_F32 && !S::F64) {
