@@ -120,6 +120,20 @@ def test_batch_calls_reject_a_null_batch(lib):
     assert lib.dugks_batch_size(None) == -1
 
 
+def test_row_calls_reject_a_null_handle(lib):
+    """The row copies and row reductions of the slab decomposition check
+    their handle and buffers before any device work."""
+    import numpy as np
+
+    buf = np.zeros(6)
+    p = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    had = ctypes.c_int32()
+    assert lib.dugks_reduce_rows(None, 0, 1, p, ctypes.byref(had)) == -1
+    assert lib.dugks_get_rows(None, 0, 1, buf.ctypes.data_as(ctypes.c_void_p), 0) == -1
+    assert lib.dugks_set_rows(None, 0, 1, buf.ctypes.data_as(ctypes.c_void_p), 0) == -1
+    assert lib.dugks_state_element_bytes(None) == 0
+
+
 def test_status_strings_cover_every_code(lib):
     for code, name in solver.STATUS.items():
         text = lib.dugks_status_string(code).decode()
