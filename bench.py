@@ -140,8 +140,8 @@ class ClockSampler:
 
 
 class NvmlSampler:
-    """SM clock and clock-event reasons read through NVML (the driver's
-    libnvidia-ml, via ctypes; reads only) every `period` seconds from a thread
+    """SM clock and clock-event reasons read through NVML (the NVIDIA
+    driver's libnvidia-ml, via ctypes; reads only) every `period` seconds from a thread
     while the GPU runs, so that even a few milliseconds of timed steps give
     many samples.  Falls back to ClockSampler (nvidia-smi) if NVML cannot be
     loaded.  The device is found by the PCI bus id torch reports."""
