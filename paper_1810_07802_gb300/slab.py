@@ -185,7 +185,8 @@ class DistExchange:
     that order in one batch (so that with two periodic ranks, where both
     neighbours are one rank, the messages pair up by order; the tags do the
     same where the backend honours them).  A band at a wall of the problem
-    has no neighbour on that side."""
+    has no neighbour on that side; a single rank's periodic band is its own
+    neighbour, and its rows are copied in place."""
 
     def __init__(self, band, rank, world, group=None):
         self.band, self.rank, self.world, self.group = band, rank, world, group
@@ -195,6 +196,12 @@ class DistExchange:
 
         b = self.band
         b.pack()
+        if self.world == 1:   # a periodic problem on one rank: its own edge rows wrap around
+            if b.lo:
+                b.recv_below.copy_(b.send_up)
+                b.recv_above.copy_(b.send_down)
+            b.unpack()
+            return
         up, down = (self.rank + 1) % self.world, (self.rank - 1) % self.world
         ops = []
         if b.hi:

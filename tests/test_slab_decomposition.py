@@ -156,8 +156,8 @@ def _assert_same_reductions(got, want):
     assert got[0][1] == 1.0 and got[1][1] < 1.0
 
 
-@pytest.mark.parametrize("world,kind", [(2, "periodic"), (3, "periodic"), (2, "wall"), (3, "wall_upwind"),
-                                        (2, "upwind")])
+@pytest.mark.parametrize("world,kind", [(1, "periodic"), (1, "wall"), (2, "periodic"), (3, "periodic"),
+                                        (2, "wall"), (3, "wall_upwind"), (2, "upwind")])
 def test_slabs_with_halo_exchange_equal_the_single_domain(world, kind):
     """gloo ranks, one band each: the bands' own rows and their all-reduced
     reductions equal the single-domain oracle's, bit for bit (the reductions
