@@ -3,8 +3,9 @@ walled in y), each a Solver on its rows plus two halo rows (three with the
 upwind reconstruction) on each side that has a neighbour, their halo rows
 refreshed before every step through dugks_get_rows / dugks_set_rows (device
 buffers, exchanged in one process).  (With one GPU per box the same bands over NCCL
-between GPUs are not run here; the exchange protocol on ranks is covered with
-gloo in test_slab_decomposition, bit for bit against the oracle.)
+between GPUs are not run here: one rank on the NCCL backend is, and the
+exchange protocol on several ranks is covered with gloo in
+test_slab_decomposition, bit for bit against the oracle.)
 
 On the GPU a cell's result depends on where the tile grid falls at the
 round-off level: the same problem shifted cyclically by three rows and
@@ -226,3 +227,44 @@ def test_band_reductions_equal_the_single_domain(S):
         assert ru == pytest.approx(ru0, rel=1e-9)
         assert um == pytest.approx(um0, rel=1e-12)
     assert got[0][1] == 1.0 and got[1][1] < 1.0
+
+
+def test_one_rank_over_nccl_equals_the_single_domain(S):
+    """DistExchange on the NCCL backend with one rank (the one GPU of the
+    box): the periodic band is its own neighbour, its halo rows come from its
+    own edge rows, and the reductions are all-reduced as CUDA tensors.  The
+    band equals the single-domain solver to round-off, and so do its
+    reductions.  (Exchanges between GPUs need more than one.)"""
+    import datetime
+    import socket
+
+    import torch.distributed as dist
+
+    from paper_1810_07802_gb300 import slab
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cfg, f = W.random_state(150, 70, seed=31, rho_ratio=100.0)
+    with S.Solver(cfg, **f) as whole:
+        whole.step(7)
+        want = whole.reduce()
+        ref = whole.distributions()
+    dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        bcfg, bfields = slab.band_problem(cfg, f, 0, cfg["ny"])
+        band = slab.Band(S.Solver(bcfg, **bfields), 0, cfg["ny"], cfg)
+        ex = slab.DistExchange(band, 0, 1)
+        slab.step_bands(ex, [band], 7)
+        got = ex.reduce()
+        dists = band.stepper.distributions()
+        band.stepper.close()
+    finally:
+        dist.destroy_process_group()
+    worst = max(float(np.abs(g[:, band.own] - r).max()) for g, r in zip(dists, ref))
+    assert worst <= ROUNDOFF["fp64"], worst
+    m, rp, ru, um = got
+    assert m == pytest.approx(want[0], rel=1e-13)
+    assert rp == 1.0 and ru == 1.0
+    assert um == pytest.approx(want[3], rel=1e-12)
