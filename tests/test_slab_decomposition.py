@@ -157,7 +157,7 @@ def _assert_same_reductions(got, want):
 
 
 @pytest.mark.parametrize("world,kind", [(1, "periodic"), (1, "wall"), (2, "periodic"), (3, "periodic"),
-                                        (2, "wall"), (3, "wall_upwind"), (2, "upwind")])
+                                        (2, "wall"), (3, "wall_upwind"), (4, "wall_upwind"), (2, "upwind")])
 def test_slabs_with_halo_exchange_equal_the_single_domain(world, kind):
     """gloo ranks, one band each: the bands' own rows and their all-reduced
     reductions equal the single-domain oracle's, bit for bit (the reductions
